@@ -1,0 +1,275 @@
+// bn_internal.cuh -- device helpers and launch descriptors shared by the
+// binning kernels (Sec. 4.2 data binning) and the host runtime.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/binning.h"
+
+namespace bn {
+
+constexpr int kMaxAttr = BN_MAX_ATTR;
+
+// ---------------------------------------------------------------- sum modes
+enum SumMode : int { kSumF32C = 0, kSumF32 = 1, kSumF64 = 2 };
+
+// ---------------------------------------------------------------- mesh axis
+// One axis of the mesh with bounds and scale already rounded to the
+// coordinate type T (stored widened in double). closed = automatic bounds.
+struct AxisDesc {
+    double lo, hi, s;
+    int32_t res;
+    int32_t closed;
+    // f64 coordinates only: 1 when the FP32 estimate of t is within one bin
+    // of the exact t everywhere on the axis (then the edge-key correction
+    // below is exact); 0 = evaluate the reference sequence on the FP64 pipe.
+    int32_t fast;
+    int32_t pad;
+};
+
+// The mesh as the kernels see it. For explicit bounds the host fills it;
+// for automatic bounds the bounds kernel writes it into device memory and
+// sets valid (0 = degenerate: the request fails, nothing is binned).
+struct GridDesc {
+    AxisDesc ax[2];
+    int32_t valid;
+    int32_t pad;
+    // Exact bin-edge keys for f64 coordinates (see EdgeTables): device
+    // pointers to res+1 ordered keys per axis, or nullptr.
+    const long long* edges[2];
+};
+
+// ---------------------------------------------------------------- columns
+template <typename T>
+struct Columns {
+    const T* x;
+    const T* y;
+    const T* a[kMaxAttr];
+    int64_t n;
+};
+
+// Per-bin state in global memory; these are the output buffers themselves
+// (or library scratch standing in for outputs the caller did not ask for).
+struct StateDesc {
+    unsigned long long* count;
+    double* sum[kMaxAttr];
+    void* mn[kMaxAttr];
+    void* mx[kMaxAttr];
+    double* avg[kMaxAttr];
+    int64_t bins;
+    int32_t n_attrs;
+    int32_t do_sum;  // sums needed (SUM or AVG requested)
+    int32_t do_min;
+    int32_t do_max;
+    int32_t do_avg;
+    int32_t pad;
+};
+
+// ---------------------------------------------------------------- bits
+__device__ __forceinline__ bool is_nan_bits(float v) {
+    return (__float_as_uint(v) & 0x7fffffffu) > 0x7f800000u;
+}
+__device__ __forceinline__ bool is_nan_bits(double v) {
+    return ((unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull) >
+           0x7ff0000000000000ull;
+}
+
+// Ordered integer key of an IEEE value: key(a) < key(b) iff a < b for
+// non-NaN a, b, with -0 and +0 both mapped to key 0 (they compare equal).
+__device__ __forceinline__ long long ordered_key(double v) {
+    long long b = __double_as_longlong(v);
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ int ordered_key(float v) {
+    int b = __float_as_int(v);
+    if (b == (int)0x80000000u) b = 0;
+    return b >= 0 ? b : (b ^ 0x7fffffff);
+}
+
+// ---------------------------------------------------------------- min / max
+// IEEE totalOrder min/max through integer atomics on the value's own bits:
+// non-negative values (sign bit 0) order like signed integers, negative
+// values order reversed like unsigned integers, and every negative bit
+// pattern is above every non-negative one as unsigned. So a min with a
+// non-negative value is a signed atomicMin and a min with a negative value
+// is an unsigned atomicMax (and the mirror image for max). Works in shared
+// and global memory; the location must hold a non-NaN value (init +/-inf).
+__device__ __forceinline__ void atomic_min_total(float* p, float v) {
+    int b = __float_as_int(v);
+    if (b >= 0) atomicMin(reinterpret_cast<int*>(p), b);
+    else atomicMax(reinterpret_cast<unsigned int*>(p), static_cast<unsigned int>(b));
+}
+__device__ __forceinline__ void atomic_max_total(float* p, float v) {
+    int b = __float_as_int(v);
+    if (b >= 0) atomicMax(reinterpret_cast<int*>(p), b);
+    else atomicMin(reinterpret_cast<unsigned int*>(p), static_cast<unsigned int>(b));
+}
+__device__ __forceinline__ void atomic_min_total(double* p, double v) {
+    long long b = __double_as_longlong(v);
+    if (b >= 0) atomicMin(reinterpret_cast<long long*>(p), b);
+    else atomicMax(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(b));
+}
+__device__ __forceinline__ void atomic_max_total(double* p, double v) {
+    long long b = __double_as_longlong(v);
+    if (b >= 0) atomicMax(reinterpret_cast<long long*>(p), b);
+    else atomicMin(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(b));
+}
+
+// totalOrder "a < b" for non-NaN a, b on the value bits (integer pipe only).
+__device__ __forceinline__ bool total_less(float a, float b) {
+    int ia = __float_as_int(a), ib = __float_as_int(b);
+    int ka = ia >= 0 ? ia : (ia ^ 0x7fffffff);
+    int kb = ib >= 0 ? ib : (ib ^ 0x7fffffff);
+    return ka < kb;
+}
+__device__ __forceinline__ bool total_less(double a, double b) {
+    long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    long long ka = ia >= 0 ? ia : (ia ^ 0x7fffffffffffffffll);
+    long long kb = ib >= 0 ? ib : (ib ^ 0x7fffffffffffffffll);
+    return ka < kb;
+}
+
+template <typename T> __device__ __forceinline__ T pos_inf();
+template <> __device__ __forceinline__ float pos_inf<float>() { return __int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ double pos_inf<double>() {
+    return __longlong_as_double(0x7ff0000000000000ll);
+}
+template <typename T> __device__ __forceinline__ T neg_inf();
+template <> __device__ __forceinline__ float neg_inf<float>() { return __int_as_float(0xff800000); }
+template <> __device__ __forceinline__ double neg_inf<double>() {
+    return __longlong_as_double((long long)0xfff0000000000000ull);
+}
+
+// ---------------------------------------------------------------- bin index
+// Axis in the coordinate's own type, prepared once per thread.
+template <typename T>
+struct Axis {
+    T lo, hi, s;
+    int res;
+    bool closed;
+};
+
+template <typename T>
+__device__ __forceinline__ Axis<T> make_axis(const AxisDesc& d) {
+    Axis<T> a;
+    a.lo = (T)d.lo;
+    a.hi = (T)d.hi;
+    a.s = (T)d.s;
+    a.res = d.res;
+    a.closed = d.closed != 0;
+    return a;
+}
+
+// The reference sequence (Sec. 4.2 bin location, rounding fixed as
+// t = RN(RN(x - lo) * s), i = min(trunc(t), res - 1)), in f32.
+__device__ __forceinline__ int axis_bin(const Axis<float>& a, float x) {
+    bool inside = a.closed ? (a.lo <= x && x <= a.hi) : (a.lo <= x && x < a.hi);
+    if (!inside) return -1;
+    float t = __fmul_rn(__fsub_rn(x, a.lo), a.s);
+    int k = __float2int_rz(t);
+    return min(k, a.res - 1);
+}
+
+// Same sequence for f64, evaluated directly on the FP64 pipe.
+__device__ __forceinline__ int axis_bin_direct(double lo, double hi, double s, int res,
+                                               bool closed, double x) {
+    bool inside = closed ? (lo <= x && x <= hi) : (lo <= x && x < hi);
+    if (!inside) return -1;
+    double t = __dmul_rn(__dsub_rn(x, lo), s);
+    int k = __double2int_rz(t);
+    return min(k, res - 1);
+}
+
+// Inverse of ordered_key(double).
+__host__ __device__ __forceinline__ double key_to_double(long long k) {
+    long long b = k >= 0 ? k : (k ^ 0x7fffffffffffffffll);
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double d;
+    memcpy(&d, &b, sizeof d);
+    return d;
+#endif
+}
+
+// FP32 approximation of a double from its top 32 bits, integer pipe only:
+// the magnitude is truncated to 20 mantissa bits (relative error < 2^-20);
+// |x| < 2^-126 becomes +/-0 and |x| >= 2^128 becomes +/-inf.
+__device__ __forceinline__ float approx_float(double x) {
+    unsigned int hi32 = (unsigned int)((unsigned long long)__double_as_longlong(x) >> 32);
+    unsigned int mag = hi32 & 0x7fffffffu;
+    unsigned int sign = hi32 & 0x80000000u;
+    if (mag < (897u << 20)) return __uint_as_float(sign);
+    if (mag >= (1151u << 20)) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((mag - (896u << 20)) << 3));
+}
+
+// f64 axis for the exact edge-key method. idx(x) = min(trunc(RN(RN(x-lo)*s)),
+// res-1) is non-decreasing in x, so bin i is the key interval
+// [E[i], E[i+1]) where E[i] is the smallest ordered key whose value has
+// idx >= i (E[0] = key(lo); E[res] = key(hi), plus one when closed). The
+// kernel estimates i in FP32, then moves it by at most one bin so that
+// E[i] <= key(x) < E[i+1]: the same index as the reference sequence, with
+// no FP64 arithmetic.
+struct AxisF64 {
+    const long long* E;
+    long long klo, khi;  // E[0], E[res]
+    float flo, fs;       // FP32 estimate parameters
+    int res;
+    bool fast;
+    double lo, hi, s;
+    bool closed;
+};
+
+__device__ __forceinline__ AxisF64 make_axis_f64(const AxisDesc& d, const long long* E) {
+    AxisF64 a;
+    a.E = E;
+    a.res = d.res;
+    a.fast = d.fast != 0 && E != nullptr;
+    a.lo = d.lo;
+    a.hi = d.hi;
+    a.s = d.s;
+    a.closed = d.closed != 0;
+    a.flo = approx_float(d.lo);
+    a.fs = (float)d.s;
+    a.klo = a.fast ? __ldg(E) : 0;
+    a.khi = a.fast ? __ldg(E + d.res) : 0;
+    return a;
+}
+
+__device__ __forceinline__ int axis_bin(const AxisF64& a, double x) {
+    if (!a.fast) return axis_bin_direct(a.lo, a.hi, a.s, a.res, a.closed, x);
+    long long k = ordered_key(x);
+    if (k < a.klo || k >= a.khi) return -1;  // NaN keys fall outside too
+    float t = __fmul_rn(__fsub_rn(approx_float(x), a.flo), a.fs);
+    int i = __float2int_rz(t);
+    i = max(0, min(i, a.res - 1));
+    if (k < __ldg(a.E + i)) {
+        i -= 1;
+    } else if (k >= __ldg(a.E + i + 1)) {
+        i += 1;
+    }
+    i = max(0, min(i, a.res - 1));
+    if (k < __ldg(a.E + i) || k >= __ldg(a.E + i + 1)) {
+        // Not expected when `fast` holds; binary search keeps the result exact.
+        int lo = 0, hi = a.res;  // E[lo] <= k < E[hi]
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (k >= __ldg(a.E + mid)) lo = mid; else hi = mid;
+        }
+        i = lo;
+    }
+    return i;
+}
+
+// ---------------------------------------------------------------- launch info
+struct LaunchCfg {
+    int grid;
+    int block;
+    size_t smem;
+};
+
+}  // namespace bn

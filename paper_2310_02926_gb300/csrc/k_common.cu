@@ -1,0 +1,383 @@
+// k_common.cu -- the small kernels around the binning hot loop:
+//   init of the per-bin state, automatic bounds (Sec. 4.2: mesh bounds
+//   "obtained on the fly" as the min/max of the coordinates), mesh set-up
+//   with exact f64 bin-edge keys, finalisation (avg = sum / count), the
+//   merge of partial results of one mesh, and a strided-column gather.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "bn_internal.cuh"
+#include "bn_kernels.h"
+
+namespace bn {
+
+// ------------------------------------------------------------------ init
+// Empty-bin state: count 0, sum +0.0, min +inf, max -inf.
+template <typename T>
+__global__ void k_init_state(StateDesc st, T* bounds_acc) {
+    const int64_t B = st.bins;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (bounds_acc && t0 == 0) {
+        bounds_acc[0] = pos_inf<T>();
+        bounds_acc[1] = neg_inf<T>();
+        bounds_acc[2] = pos_inf<T>();
+        bounds_acc[3] = neg_inf<T>();
+    }
+    for (int64_t b = t0; b < B; b += stride) st.count[b] = 0ull;
+    for (int a = 0; a < st.n_attrs; ++a) {
+        if (st.do_sum)
+            for (int64_t b = t0; b < B; b += stride) st.sum[a][b] = 0.0;
+        if (st.do_min) {
+            T* p = static_cast<T*>(st.mn[a]);
+            for (int64_t b = t0; b < B; b += stride) p[b] = pos_inf<T>();
+        }
+        if (st.do_max) {
+            T* p = static_cast<T*>(st.mx[a]);
+            for (int64_t b = t0; b < B; b += stride) p[b] = neg_inf<T>();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ bounds
+template <typename T> struct KeyT;
+template <> struct KeyT<float> { using type = int; };
+template <> struct KeyT<double> { using type = long long; };
+
+template <typename T>
+__device__ __forceinline__ bool finite_bits(T v);
+template <> __device__ __forceinline__ bool finite_bits<float>(float v) {
+    return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
+}
+template <> __device__ __forceinline__ bool finite_bits<double>(double v) {
+    return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) !=
+           0x7ff0000000000000ull;
+}
+
+// min/max over the finite values of x and y, reduced with ordered integer
+// keys (no FP compares), one atomic per warp into bounds_acc[4] =
+// {min x, max x, min y, max y}.
+template <typename T>
+__global__ void k_bounds_reduce(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
+                                T* bounds_acc) {
+    using K = typename KeyT<T>::type;
+    const K kmax = (K)(~(typename std::make_unsigned<K>::type)0 >> 1);
+    const K kmin = -kmax - 1;
+    K mnx = kmax, mxx = kmin, mny = kmax, mxy = kmin;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        T vx = x[i], vy = y[i];
+        if (finite_bits(vx)) {
+            K k = ordered_key(vx);
+            mnx = min(mnx, k);
+            mxx = max(mxx, k);
+        }
+        if (finite_bits(vy)) {
+            K k = ordered_key(vy);
+            mny = min(mny, k);
+            mxy = max(mxy, k);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        mnx = min(mnx, __shfl_xor_sync(0xffffffffu, mnx, off));
+        mxx = max(mxx, __shfl_xor_sync(0xffffffffu, mxx, off));
+        mny = min(mny, __shfl_xor_sync(0xffffffffu, mny, off));
+        mxy = max(mxy, __shfl_xor_sync(0xffffffffu, mxy, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        // keys back to values; a key of kmax/kmin means "no finite value seen"
+        auto val = [](K k) -> T {
+            if (sizeof(T) == 8) return (T)key_to_double((long long)k);
+            int b = (int)k >= 0 ? (int)k : ((int)k ^ 0x7fffffff);
+            return (T)__int_as_float(b);
+        };
+        if (mnx != kmax) atomic_min_total(&bounds_acc[0], val(mnx));
+        if (mxx != kmin) atomic_max_total(&bounds_acc[1], val(mxx));
+        if (mny != kmax) atomic_min_total(&bounds_acc[2], val(mny));
+        if (mxy != kmin) atomic_max_total(&bounds_acc[3], val(mxy));
+    }
+}
+
+// ------------------------------------------------------------------ set-up
+// Reference bin index on the FP64 pipe (used only to locate edges).
+__device__ __forceinline__ int ref_idx_f64(const AxisDesc& d, double x) {
+    double t = __dmul_rn(__dsub_rn(x, d.lo), d.s);
+    int k = __double2int_rz(t);
+    return min(k, d.res - 1);
+}
+
+__device__ __forceinline__ long long key_of(double v) { return ordered_key(v); }
+
+// E[i]: the smallest ordered key whose value has bin index >= i. The index
+// is non-decreasing in the key, so a bracketing search finds it; it starts
+// at the key of lo + i / s and gallops outwards.
+__device__ long long edge_key(const AxisDesc& d, int i) {
+    const long long K0 = key_of(d.lo);
+    const long long Khi = key_of(d.hi) + (d.closed ? 1 : 0);
+    if (i <= 0) return K0;
+    if (i >= d.res) return Khi;
+    // invariant: f(lo_k) false (index < i), f(hi_k) true (index >= i; Khi by
+    // convention since hi itself indexes to res - 1 >= i)
+    long long lo_k = K0, hi_k = Khi;
+    auto f = [&](long long k) { return ref_idx_f64(d, key_to_double(k)) >= i; };
+    auto gap = [&]() { return (unsigned long long)hi_k - (unsigned long long)lo_k; };
+    if (gap() > 2) {
+        double est = __dadd_rn(d.lo, __ddiv_rn((double)i, d.s));
+        long long e = key_of(est);
+        if (e <= lo_k) e = lo_k + 1;
+        if (e >= hi_k) e = hi_k - 1;
+        if (f(e)) {
+            hi_k = e;
+            unsigned long long step = 1;
+            for (int it = 0; it < 64 && gap() > 1; ++it) {
+                if (step >= gap()) break;
+                long long c = hi_k - (long long)step;
+                if (f(c)) { hi_k = c; step <<= 1; } else { lo_k = c; break; }
+            }
+        } else {
+            lo_k = e;
+            unsigned long long step = 1;
+            for (int it = 0; it < 64 && gap() > 1; ++it) {
+                if (step >= gap()) break;
+                long long c = lo_k + (long long)step;
+                if (f(c)) { hi_k = c; break; } else { lo_k = c; step <<= 1; }
+            }
+        }
+    }
+    for (int it = 0; it < 70 && gap() > 1; ++it) {
+        long long mid = lo_k + (long long)(gap() >> 1);
+        if (f(mid)) hi_k = mid; else lo_k = mid;
+    }
+    return hi_k;
+}
+
+template <typename T>
+__device__ bool make_axis_from_bounds(T lo, T hi, int res, AxisDesc* d) {
+    // Sec. 4.2 automatic bounds: [min, max] of the finite coordinates, closed.
+    if (!finite_bits(lo) || !finite_bits(hi)) return false;
+    T width;
+    T s;
+    if (sizeof(T) == 8) {
+        width = (T)__dsub_rn((double)hi, (double)lo);
+        s = (T)__ddiv_rn((double)res, (double)width);
+    } else {
+        width = (T)__fsub_rn((float)hi, (float)lo);
+        s = (T)__fdiv_rn((float)res, (float)width);
+    }
+    if (!(width > (T)0) || !finite_bits(width) || !(s > (T)0) || !finite_bits(s)) return false;
+    d->lo = (double)lo;
+    d->hi = (double)hi;
+    d->s = (double)s;
+    d->res = res;
+    d->closed = 1;
+    return true;
+}
+
+// The FP32 estimate of t is off by at most about (|x| + |lo|) * s * 2^-19
+// plus a few FP32 roundings of t; when that stays below half a bin the
+// one-step edge correction is exact.
+__device__ __host__ inline int fast_ok(double lo, double hi, double s, int res) {
+    double m = fabs(lo) > fabs(hi) ? fabs(lo) : fabs(hi);
+    double err = 2.0 * m * s * (1.0 / 524288.0) + (double)res * (1.0 / 2097152.0);
+    return (err < 0.25 && m < 1e37 && s < 1e37) ? 1 : 0;
+}
+
+// One block computes the mesh (automatic bounds: from bounds_acc; explicit:
+// from the host's descriptor); every block then fills a slice of the f64
+// edge tables. Block 0 publishes the descriptor, the bounds actually used
+// and, if the automatic bounds collapsed, BN_ERR_DEGENERATE in *status.
+template <typename T>
+__global__ void k_grid_setup(GridDesc host_desc, const T* bounds_acc, GridDesc* dev_desc,
+                             long long* edges0, long long* edges1, double* bounds_out,
+                             int* status) {
+    __shared__ GridDesc g;
+    if (threadIdx.x == 0) {
+        g = host_desc;
+        if (bounds_acc) {
+            bool ok = make_axis_from_bounds<T>(bounds_acc[0], bounds_acc[1], host_desc.ax[0].res,
+                                               &g.ax[0]) &&
+                      make_axis_from_bounds<T>(bounds_acc[2], bounds_acc[3], host_desc.ax[1].res,
+                                               &g.ax[1]);
+            g.valid = ok ? 1 : 0;
+        }
+        for (int a = 0; a < 2; ++a)
+            g.ax[a].fast = (sizeof(T) == 8 && g.valid)
+                               ? fast_ok(g.ax[a].lo, g.ax[a].hi, g.ax[a].s, g.ax[a].res)
+                               : 0;
+        g.edges[0] = (sizeof(T) == 8) ? edges0 : nullptr;
+        g.edges[1] = (sizeof(T) == 8) ? edges1 : nullptr;
+        if (blockIdx.x == 0) {
+            *dev_desc = g;
+            if (!g.valid && status) *status = BN_ERR_DEGENERATE;
+            if (bounds_out && g.valid) {
+                bounds_out[0] = g.ax[0].lo;
+                bounds_out[1] = g.ax[0].hi;
+                bounds_out[2] = g.ax[1].lo;
+                bounds_out[3] = g.ax[1].hi;
+            }
+        }
+    }
+    __syncthreads();
+    if (sizeof(T) != 8 || !g.valid) return;
+    const int n0 = g.ax[0].res + 1, n1 = g.ax[1].res + 1;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n0 + n1; j += gridDim.x * blockDim.x) {
+        if (j < n0) edges0[j] = edge_key(g.ax[0], j);
+        else edges1[j - n0] = edge_key(g.ax[1], j - n0);
+    }
+}
+
+// ------------------------------------------------------------------ finalise
+// avg = sum / count in FP64 (round-to-nearest division); empty bins get the
+// quiet NaN 0x7ff8000000000000.
+__global__ void k_finalize(StateDesc st) {
+    const int64_t B = st.bins;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += stride) {
+        unsigned long long c = st.count[b];
+        double dc = (double)c;
+        for (int a = 0; a < st.n_attrs; ++a)
+            st.avg[a][b] = c ? __ddiv_rn(st.sum[a][b], dc) : qnan;
+    }
+}
+
+// ------------------------------------------------------------------ merge
+// Combine finalized results of one mesh (the cross-rank merge implied by
+// MPI-parallel binning, Sec. 4.2): count and sum add, min/max combine in
+// totalOrder. avg is recomputed by k_finalize afterwards.
+template <typename T>
+__global__ void k_merge(StateDesc out, const StateDesc* parts, int n_parts) {
+    const int64_t B = out.bins;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += stride) {
+        unsigned long long c = 0;
+        for (int p = 0; p < n_parts; ++p) c += parts[p].count[b];
+        out.count[b] = c;
+        for (int a = 0; a < out.n_attrs; ++a) {
+            if (out.do_sum) {
+                double s = 0.0;
+                for (int p = 0; p < n_parts; ++p) s = __dadd_rn(s, parts[p].sum[a][b]);
+                out.sum[a][b] = s;
+            }
+            if (out.do_min) {
+                T m = pos_inf<T>();
+                for (int p = 0; p < n_parts; ++p) {
+                    T v = static_cast<const T*>(parts[p].mn[a])[b];
+                    if (total_less(v, m)) m = v;
+                }
+                static_cast<T*>(out.mn[a])[b] = m;
+            }
+            if (out.do_max) {
+                T m = neg_inf<T>();
+                for (int p = 0; p < n_parts; ++p) {
+                    T v = static_cast<const T*>(parts[p].mx[a])[b];
+                    if (total_less(m, v)) m = v;
+                }
+                static_cast<T*>(out.mx[a])[b] = m;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ gather
+template <typename T>
+__global__ void k_gather(T* __restrict__ dst, const T* __restrict__ src, int64_t n, int64_t stride) {
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step)
+        dst[i] = src[i * stride];
+}
+
+// ------------------------------------------------------------------ launchers
+static inline int grid_for(int64_t work, int block, int max_blocks) {
+    int64_t g = (work + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+cudaError_t launch_init_state(const KernelCtx& kc, int dtype, const StateDesc& st,
+                              void* bounds_acc) {
+    const int block = 256;
+    int grid = grid_for(st.bins, block, kc.num_sms * 8);
+    if (dtype == BN_F64)
+        k_init_state<double><<<grid, block, 0, kc.stream>>>(st, static_cast<double*>(bounds_acc));
+    else
+        k_init_state<float><<<grid, block, 0, kc.stream>>>(st, static_cast<float*>(bounds_acc));
+    kc.count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounds_reduce(const KernelCtx& kc, int dtype, const void* x, const void* y,
+                                 int64_t n, void* bounds_acc) {
+    const int block = 256;
+    int grid = grid_for(n, block, kc.num_sms * 8);
+    if (dtype == BN_F64)
+        k_bounds_reduce<double><<<grid, block, 0, kc.stream>>>(
+            static_cast<const double*>(x), static_cast<const double*>(y), n,
+            static_cast<double*>(bounds_acc));
+    else
+        k_bounds_reduce<float><<<grid, block, 0, kc.stream>>>(
+            static_cast<const float*>(x), static_cast<const float*>(y), n,
+            static_cast<float*>(bounds_acc));
+    kc.count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_setup(const KernelCtx& kc, int dtype, const GridDesc& host_desc,
+                              const void* bounds_acc, GridDesc* dev_desc, long long* edges0,
+                              long long* edges1, double* bounds_out, int* status) {
+    const int block = 128;
+    int grid = 1;
+    if (dtype == BN_F64) {
+        int64_t n_edges = (int64_t)host_desc.ax[0].res + host_desc.ax[1].res + 2;
+        grid = grid_for(n_edges, block, kc.num_sms * 4);
+        k_grid_setup<double><<<grid, block, 0, kc.stream>>>(
+            host_desc, static_cast<const double*>(bounds_acc), dev_desc, edges0, edges1,
+            bounds_out, status);
+    } else {
+        k_grid_setup<float><<<grid, block, 0, kc.stream>>>(
+            host_desc, static_cast<const float*>(bounds_acc), dev_desc, nullptr, nullptr,
+            bounds_out, status);
+    }
+    kc.count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const KernelCtx& kc, const StateDesc& st) {
+    const int block = 256;
+    int grid = grid_for(st.bins, block, kc.num_sms * 8);
+    k_finalize<<<grid, block, 0, kc.stream>>>(st);
+    kc.count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const KernelCtx& kc, int dtype, const StateDesc& out,
+                         const StateDesc* dev_parts, int n_parts) {
+    const int block = 256;
+    int grid = grid_for(out.bins, block, kc.num_sms * 8);
+    if (dtype == BN_F64)
+        k_merge<double><<<grid, block, 0, kc.stream>>>(out, dev_parts, n_parts);
+    else
+        k_merge<float><<<grid, block, 0, kc.stream>>>(out, dev_parts, n_parts);
+    kc.count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const KernelCtx& kc, int dtype, void* dst, const void* src, int64_t n,
+                          int64_t stride) {
+    const int block = 256;
+    int grid = grid_for(n, block, kc.num_sms * 8);
+    if (dtype == BN_F64)
+        k_gather<double><<<grid, block, 0, kc.stream>>>(static_cast<double*>(dst),
+                                                        static_cast<const double*>(src), n, stride);
+    else
+        k_gather<float><<<grid, block, 0, kc.stream>>>(static_cast<float*>(dst),
+                                                       static_cast<const float*>(src), n, stride);
+    kc.count_launch();
+    return cudaGetLastError();
+}
+
+int host_fast_ok(double lo, double hi, double s, int res) { return fast_ok(lo, hi, s, res); }
+
+}  // namespace bn

@@ -1,0 +1,257 @@
+// k_global.cu -- particles straight into the global mesh with L2 atomics,
+// for meshes too large to privatise in shared memory (Sec. 4.2 binning; the
+// atomic updates whose races Sec. 4.4 names as binning's GPU cost).
+//
+// Per in-bounds particle: one u64 count add and one FP64 add per attribute
+// (executed in L2, not on the SM's FP64 pipe), and min/max atomics only
+// when a plain read of the current value shows the particle would change
+// it (min only falls and max only rises, so a stale read is safe: it can
+// only let through an atomic that turns out to be unnecessary). Lanes of a
+// warp that hit the same bin are combined first (__match_any_sync) so a
+// cluster of particles costs one set of atomics per warp, not per lane.
+#include <cuda_runtime.h>
+
+#include "bn_internal.cuh"
+#include "bn_kernels.h"
+
+namespace bn {
+
+template <typename T> struct GVec;
+template <> struct GVec<float> { using type = float4; static constexpr int N = 4; };
+template <> struct GVec<double> { using type = double2; static constexpr int N = 2; };
+
+template <typename T>
+__device__ __forceinline__ T gget(const typename GVec<T>::type& v, int j);
+template <> __device__ __forceinline__ float gget<float>(const float4& v, int j) {
+    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+template <> __device__ __forceinline__ double gget<double>(const double2& v, int j) {
+    return j == 0 ? v.x : v.y;
+}
+
+template <typename T> struct GBinner;
+template <> struct GBinner<float> {
+    Axis<float> ax, ay;
+    int rx;
+    __device__ void init(const GridDesc& g) {
+        ax = make_axis<float>(g.ax[0]);
+        ay = make_axis<float>(g.ax[1]);
+        rx = g.ax[0].res;
+    }
+    __device__ __forceinline__ int bin(float x, float y) const {
+        int ix = axis_bin(ax, x);
+        int iy = axis_bin(ay, y);
+        return (ix < 0 || iy < 0) ? -1 : iy * rx + ix;
+    }
+};
+template <> struct GBinner<double> {
+    AxisF64 ax, ay;
+    int rx;
+    __device__ void init(const GridDesc& g) {
+        ax = make_axis_f64(g.ax[0], g.edges[0]);
+        ay = make_axis_f64(g.ax[1], g.edges[1]);
+        rx = g.ax[0].res;
+    }
+    __device__ __forceinline__ int bin(double x, double y) const {
+        int ix = axis_bin(ax, x);
+        int iy = axis_bin(ay, y);
+        return (ix < 0 || iy < 0) ? -1 : iy * rx + ix;
+    }
+};
+
+// Combine the lanes of the calling warp that share bin b (b >= 0) and let
+// the lowest such lane update the global mesh. Every lane of the warp must
+// call it (b = -1 for lanes without an in-bounds particle).
+template <typename T, int A_CT>
+__device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, const T* v) {
+    const unsigned full = 0xffffffffu;
+    const unsigned peers = __match_any_sync(full, b);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    const bool alone = peers == (1u << lane);
+    if (__all_sync(full, alone || b < 0)) {
+        // no two lanes share a bin: skip the combining shuffles
+        if (b < 0) return;
+        atomicAdd(&st.count[b], 1ull);
+        for (int a = 0; a < A; ++a) {
+            const T x = v[a];
+            if (st.do_sum) atomicAdd(&st.sum[a][b], (double)x);
+            if (is_nan_bits(x)) continue;
+            if (st.do_min) {
+                T* g = static_cast<T*>(st.mn[a]) + b;
+                if (total_less(x, __ldcg(g))) atomic_min_total(g, x);
+            }
+            if (st.do_max) {
+                T* g = static_cast<T*>(st.mx[a]) + b;
+                if (total_less(__ldcg(g), x)) atomic_max_total(g, x);
+            }
+        }
+        return;
+    }
+    // General case: the leader of each peer group gathers its peers' values
+    // lane by lane (the loop runs over the largest group in the warp).
+    const unsigned cnt = __popc(peers);
+    double s[A_CT > 0 ? A_CT : kMaxAttr];
+    T lo[A_CT > 0 ? A_CT : kMaxAttr], hi[A_CT > 0 ? A_CT : kMaxAttr];
+    for (int a = 0; a < A; ++a) {
+        s[a] = 0.0;
+        lo[a] = pos_inf<T>();
+        hi[a] = neg_inf<T>();
+    }
+    unsigned rest = peers;
+    // every lane walks its own group; shuffles need all lanes, so loop to the
+    // warp-wide maximum group size
+    int my_n = (b >= 0) ? (int)cnt : 0;
+    int max_n = my_n;
+    for (int off = 16; off > 0; off >>= 1) max_n = max(max_n, __shfl_xor_sync(full, max_n, off));
+    for (int it = 0; it < max_n; ++it) {
+        int src = rest ? __ffs(rest) - 1 : lane;
+        if (rest) rest &= rest - 1;
+        for (int a = 0; a < A; ++a) {
+            T x = __shfl_sync(full, v[a], src);
+            if (b >= 0 && it < my_n) {
+                s[a] += (double)x;  // FP64 add in this lane's registers
+                if (!is_nan_bits(x)) {
+                    if (total_less(x, lo[a])) lo[a] = x;
+                    if (total_less(hi[a], x)) hi[a] = x;
+                }
+            }
+        }
+    }
+    if (b < 0 || lane != leader) return;
+    atomicAdd(&st.count[b], (unsigned long long)cnt);
+    for (int a = 0; a < A; ++a) {
+        if (st.do_sum) atomicAdd(&st.sum[a][b], s[a]);
+        if (st.do_min && !(lo[a] == pos_inf<T>())) {
+            T* g = static_cast<T*>(st.mn[a]) + b;
+            if (total_less(lo[a], __ldcg(g))) atomic_min_total(g, lo[a]);
+        }
+        if (st.do_max && !(hi[a] == neg_inf<T>())) {
+            T* g = static_cast<T*>(st.mx[a]) + b;
+            if (total_less(__ldcg(g), hi[a])) atomic_max_total(g, hi[a]);
+        }
+    }
+}
+
+template <typename T, int A_CT>
+__global__ void __launch_bounds__(256) k_bin_global(BinArgs args, int64_t head, int64_t groups) {
+    using V = typename GVec<T>::type;
+    constexpr int VN = GVec<T>::N;
+    constexpr int AC = A_CT > 0 ? A_CT : kMaxAttr;
+    const GridDesc g = args.dev_grid ? *args.dev_grid : args.grid;
+    if (!g.valid) return;
+    const int A = A_CT >= 0 ? A_CT : args.n_attrs;
+    const StateDesc& st = args.st;
+    GBinner<T> binner;
+    binner.init(g);
+
+    const T* __restrict__ X = static_cast<const T*>(args.x);
+    const T* __restrict__ Y = static_cast<const T*>(args.y);
+    const int64_t n = args.n;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+
+    // scalar head and tail: whole warps iterate together (warp_commit needs
+    // every lane), lanes past the end pass b = -1
+    const int64_t tail0 = head + groups * VN;
+    const int64_t warp_base = tid - (threadIdx.x & 31);
+    auto scalar_range = [&](int64_t r0, int64_t r1) {
+        for (int64_t base = r0 + warp_base; base < r1; base += nthreads) {
+            const int64_t i = base + (threadIdx.x & 31);
+            T v[AC];
+            int b = -1;
+            if (i < r1) {
+                b = binner.bin(X[i], Y[i]);
+                for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(args.a[a])[i];
+            }
+            warp_commit<T, A_CT>(st, A, b, v);
+        }
+    };
+    scalar_range(0, head);
+    scalar_range(tail0, n);
+
+    const V* __restrict__ XV = reinterpret_cast<const V*>(X + head);
+    const V* __restrict__ YV = reinterpret_cast<const V*>(Y + head);
+    for (int64_t gbase = warp_base; gbase < groups; gbase += nthreads) {
+        const int64_t gi = gbase + (threadIdx.x & 31);
+        const bool live = gi < groups;
+        V x0, y0;
+        V av[A_CT > 0 ? A_CT : 1];
+        if (live) {
+            x0 = __ldcs(XV + gi);
+            y0 = __ldcs(YV + gi);
+            if (A_CT > 0) {
+#pragma unroll
+                for (int a = 0; a < A_CT; ++a)
+                    av[a] = __ldcs(reinterpret_cast<const V*>(static_cast<const T*>(args.a[a]) + head) + gi);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < VN; ++j) {
+            int b = -1;
+            T v[AC];
+            if (live) {
+                b = binner.bin(gget<T>(x0, j), gget<T>(y0, j));
+                if (A_CT > 0) {
+#pragma unroll
+                    for (int a = 0; a < (A_CT > 0 ? A_CT : 1); ++a) v[a] = gget<T>(av[a], j);
+                } else {
+                    const int64_t i = head + gi * VN + j;
+                    for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(args.a[a])[i];
+                }
+            }
+            warp_commit<T, A_CT>(st, A, b, v);
+        }
+    }
+}
+
+template <typename T>
+static void gvector_split(const BinArgs& a, int64_t* head, int64_t* groups) {
+    constexpr int VN = GVec<T>::N;
+    auto phase = [](const void* p) { return (int)(((uintptr_t)p / sizeof(T)) % VN); };
+    const bool aligned = ((uintptr_t)a.x % sizeof(T)) == 0;
+    int ph = phase(a.x);
+    bool same = aligned && phase(a.y) == ph;
+    for (int k = 0; k < a.n_attrs; ++k) same = same && phase(a.a[k]) == ph;
+    if (!same) {
+        *head = a.n;
+        *groups = 0;
+        return;
+    }
+    int64_t h = (VN - ph) % VN;
+    if (h > a.n) h = a.n;
+    *head = h;
+    *groups = (a.n - h) / VN;
+}
+
+template <typename T, int A_CT>
+static cudaError_t launch_global_t(const KernelCtx& kc, const BinArgs& a) {
+    int64_t head, groups;
+    gvector_split<T>(a, &head, &groups);
+    const int block = 256;
+    int64_t work = groups > 0 ? groups : a.n;
+    int64_t grid = (work + block - 1) / block;
+    int64_t cap = (int64_t)kc.num_sms * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    k_bin_global<T, A_CT><<<(int)grid, block, 0, kc.stream>>>(a, head, groups);
+    kc.count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t dispatch_global(const KernelCtx& kc, const BinArgs& a) {
+    switch (a.n_attrs) {
+        case 1: return launch_global_t<T, 1>(kc, a);
+        case 2: return launch_global_t<T, 2>(kc, a);
+        case 3: return launch_global_t<T, 3>(kc, a);
+        case 4: return launch_global_t<T, 4>(kc, a);
+        default: return launch_global_t<T, -1>(kc, a);
+    }
+}
+
+cudaError_t launch_bin_global(const KernelCtx& kc, const BinArgs& a) {
+    return a.dtype == BN_F64 ? dispatch_global<double>(kc, a) : dispatch_global<float>(kc, a);
+}
+
+}  // namespace bn

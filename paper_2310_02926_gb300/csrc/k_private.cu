@@ -1,0 +1,392 @@
+// k_private.cu -- K1: per-CTA shared-memory copy of the whole mesh.
+//
+// Sec. 4.2 bins each particle into one mesh cell and reduces count, sum,
+// min and max per cell; the paper's CUDA version resolves races between
+// threads with atomic updates of one global mesh and calls that the reason
+// binning suits GPUs poorly (Sec. 4.4). Here each CTA owns a private copy
+// of the mesh in shared memory, so the per-particle atomics are shared-
+// memory atomics (integer count, FP add, integer min/max on IEEE bits) and
+// global atomics happen once per non-empty bin per CTA, in the merge.
+//
+// Columns are streamed with 16-byte vector loads (two groups per thread
+// per iteration, so several loads are in flight); the bin index follows
+// the reference rounding sequence exactly (f32: directly; f64: via the
+// exact edge keys, no FP64 arithmetic).
+#include <cuda_runtime.h>
+
+#include "bn_internal.cuh"
+#include "bn_kernels.h"
+
+namespace bn {
+
+template <typename T> struct VecOf;
+template <> struct VecOf<float> { using type = float4; static constexpr int N = 4; };
+template <> struct VecOf<double> { using type = double2; static constexpr int N = 2; };
+
+template <typename T>
+__device__ __forceinline__ T vget(const typename VecOf<T>::type& v, int j);
+template <> __device__ __forceinline__ float vget<float>(const float4& v, int j) {
+    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+template <> __device__ __forceinline__ double vget<double>(const double2& v, int j) {
+    return j == 0 ? v.x : v.y;
+}
+
+// Mesh location of a particle, -1 when outside.
+template <typename T> struct Binner;
+template <> struct Binner<float> {
+    Axis<float> ax, ay;
+    int rx;
+    __device__ void init(const GridDesc& g) {
+        ax = make_axis<float>(g.ax[0]);
+        ay = make_axis<float>(g.ax[1]);
+        rx = g.ax[0].res;
+    }
+    __device__ __forceinline__ int bin(float x, float y) const {
+        int ix = axis_bin(ax, x);
+        int iy = axis_bin(ay, y);
+        return (ix < 0 || iy < 0) ? -1 : iy * rx + ix;
+    }
+};
+template <> struct Binner<double> {
+    AxisF64 ax, ay;
+    int rx;
+    __device__ void init(const GridDesc& g) {
+        ax = make_axis_f64(g.ax[0], g.edges[0]);
+        ay = make_axis_f64(g.ax[1], g.edges[1]);
+        rx = g.ax[0].res;
+    }
+    __device__ __forceinline__ int bin(double x, double y) const {
+        int ix = axis_bin(ax, x);
+        int iy = axis_bin(ay, y);
+        return (ix < 0 || iy < 0) ? -1 : iy * rx + ix;
+    }
+};
+
+// Shared-memory mesh. Sums are FP64 for f64 data and for f32 data in
+// kSumF64 mode; FP32 (plus an FP32 compensation term in kSumF32C) otherwise.
+template <typename T, int MODE>
+struct SmemMesh {
+    static constexpr bool kWide = sizeof(T) == 8 || MODE == kSumF64;
+    unsigned int* cnt;
+    double* s64;
+    float* s32;
+    float* c32;
+    T* mn;
+    T* mx;
+    int B;
+    bool do_sum, do_min, do_max;
+
+    __device__ static size_t bytes(int B, int A, bool do_sum, bool do_min, bool do_max) {
+        size_t b = ((size_t)B * 4 + 15) & ~(size_t)15;
+        if (do_sum) b += (size_t)A * B * (kWide ? 8 : (MODE == kSumF32C ? 8 : 4));
+        if (do_min) b += (size_t)A * B * sizeof(T);
+        if (do_max) b += (size_t)A * B * sizeof(T);
+        return b;
+    }
+
+    __device__ void carve(unsigned char* base, int B_, int A, bool s, bool lo, bool hi) {
+        B = B_;
+        do_sum = s;
+        do_min = lo;
+        do_max = hi;
+        size_t off = ((size_t)B * 4 + 15) & ~(size_t)15;
+        cnt = reinterpret_cast<unsigned int*>(base);
+        s64 = nullptr;
+        s32 = nullptr;
+        c32 = nullptr;
+        if (do_sum) {
+            if (kWide) {
+                s64 = reinterpret_cast<double*>(base + off);
+                off += (size_t)A * B * 8;
+            } else {
+                s32 = reinterpret_cast<float*>(base + off);
+                off += (size_t)A * B * 4;
+                if (MODE == kSumF32C) {
+                    c32 = reinterpret_cast<float*>(base + off);
+                    off += (size_t)A * B * 4;
+                }
+            }
+        }
+        mn = do_min ? reinterpret_cast<T*>(base + off) : nullptr;
+        if (do_min) off += (size_t)A * B * sizeof(T);
+        mx = do_max ? reinterpret_cast<T*>(base + off) : nullptr;
+    }
+
+    __device__ void clear(int A) {
+        for (int b = threadIdx.x; b < B; b += blockDim.x) cnt[b] = 0u;
+        const int AB = A * B;
+        if (do_sum) {
+            if (kWide) {
+                for (int k = threadIdx.x; k < AB; k += blockDim.x) s64[k] = 0.0;
+            } else {
+                for (int k = threadIdx.x; k < AB; k += blockDim.x) s32[k] = 0.0f;
+                if (MODE == kSumF32C)
+                    for (int k = threadIdx.x; k < AB; k += blockDim.x) c32[k] = 0.0f;
+            }
+        }
+        if (do_min)
+            for (int k = threadIdx.x; k < AB; k += blockDim.x) mn[k] = pos_inf<T>();
+        if (do_max)
+            for (int k = threadIdx.x; k < AB; k += blockDim.x) mx[k] = neg_inf<T>();
+    }
+
+    __device__ __forceinline__ void add_count(int b) { atomicAdd(&cnt[b], 1u); }
+
+    __device__ __forceinline__ void add(int a, int b, T v) {
+        const int k = a * B + b;
+        if (do_sum) {
+            if (kWide) {
+                atomicAdd(&s64[k], (double)v);
+            } else if (MODE == kSumF32) {
+                atomicAdd(&s32[k], (float)v);
+            } else {
+                // Two-sum of the value the atomic added to: the exact rounding
+                // error of old + v goes into the compensation term.
+                float fv = (float)v;
+                float old = atomicAdd(&s32[k], fv);
+                float s = __fadd_rn(old, fv);
+                float bp = __fsub_rn(s, old);
+                float err = __fadd_rn(__fsub_rn(old, __fsub_rn(s, bp)), __fsub_rn(fv, bp));
+                // once the sum is +/-inf or NaN the error term is meaningless
+                // (inf - inf); the sum itself already carries the result
+                if (err != 0.0f && (__float_as_uint(err) & 0x7f800000u) != 0x7f800000u)
+                    atomicAdd(&c32[k], err);
+            }
+        }
+        if (is_nan_bits(v)) return;
+        if (do_min && total_less(v, mn[k])) atomic_min_total(&mn[k], v);
+        if (do_max && total_less(mx[k], v)) atomic_max_total(&mx[k], v);
+    }
+
+    // CTA partial -> global mesh, once per non-empty bin.
+    __device__ void merge(const StateDesc& st, int A) {
+        for (int b = threadIdx.x; b < B; b += blockDim.x) {
+            unsigned int c = cnt[b];
+            if (c == 0u) continue;
+            atomicAdd(&st.count[b], (unsigned long long)c);
+            for (int a = 0; a < A; ++a) {
+                const int k = a * B + b;
+                if (do_sum) {
+                    double v;
+                    if (kWide) v = s64[k];
+                    else if (MODE == kSumF32) v = (double)s32[k];
+                    else {
+                        const float hi = s32[k];
+                        v = ((__float_as_uint(hi) & 0x7f800000u) == 0x7f800000u)
+                                ? (double)hi
+                                : __dadd_rn((double)hi, (double)c32[k]);
+                    }
+                    atomicAdd(&st.sum[a][b], v);
+                }
+                if (do_min) {
+                    T m = mn[k];
+                    T* g = static_cast<T*>(st.mn[a]) + b;
+                    if (total_less(m, __ldcg(g))) atomic_min_total(g, m);
+                }
+                if (do_max) {
+                    T m = mx[k];
+                    T* g = static_cast<T*>(st.mx[a]) + b;
+                    if (total_less(__ldcg(g), m)) atomic_max_total(g, m);
+                }
+            }
+        }
+    }
+};
+
+template <typename T, int A_CT, int MODE>
+__global__ void __launch_bounds__(512) k_bin_private(BinArgs args, int64_t head, int64_t groups) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::N;
+    const GridDesc g = args.dev_grid ? *args.dev_grid : args.grid;
+    if (!g.valid) return;
+    const int A = A_CT >= 0 ? A_CT : args.n_attrs;
+    const int B = g.ax[0].res * g.ax[1].res;
+    const StateDesc& st = args.st;
+
+    SmemMesh<T, MODE> m;
+    m.carve(smem, B, A, st.do_sum != 0, st.do_min != 0, st.do_max != 0);
+    m.clear(A);
+    Binner<T> binner;
+    binner.init(g);
+    __syncthreads();
+
+    const T* __restrict__ X = static_cast<const T*>(args.x);
+    const T* __restrict__ Y = static_cast<const T*>(args.y);
+    const int64_t n = args.n;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+
+    auto one = [&](int64_t i) {
+        int b = binner.bin(X[i], Y[i]);
+        if (b < 0) return;
+        m.add_count(b);
+        for (int a = 0; a < A; ++a) m.add(a, b, static_cast<const T*>(args.a[a])[i]);
+    };
+
+    // scalar head (until every column is 16-byte aligned) and tail
+    const int64_t tail0 = head + groups * VN;
+    for (int64_t i = tid; i < head; i += nthreads) one(i);
+    for (int64_t i = tail0 + tid; i < n; i += nthreads) one(i);
+
+    // vector body: groups of VN particles, two groups per thread per step
+    const V* __restrict__ XV = reinterpret_cast<const V*>(X + head);
+    const V* __restrict__ YV = reinterpret_cast<const V*>(Y + head);
+    if (A_CT >= 0) {
+        constexpr int AC = A_CT > 0 ? A_CT : 1;
+        const V* AV[AC];
+#pragma unroll
+        for (int a = 0; a < AC; ++a)
+            AV[a] = reinterpret_cast<const V*>(static_cast<const T*>(args.a[a < A ? a : 0]) + head);
+        int64_t gi = tid;
+        for (; gi + nthreads < groups; gi += 2 * nthreads) {
+            V x0 = __ldcs(XV + gi), y0 = __ldcs(YV + gi);
+            V x1 = __ldcs(XV + gi + nthreads), y1 = __ldcs(YV + gi + nthreads);
+            V a0[AC], a1[AC];
+#pragma unroll
+            for (int a = 0; a < A_CT; ++a) {
+                a0[a] = __ldcs(AV[a] + gi);
+                a1[a] = __ldcs(AV[a] + gi + nthreads);
+            }
+#pragma unroll
+            for (int j = 0; j < VN; ++j) {
+                int b = binner.bin(vget<T>(x0, j), vget<T>(y0, j));
+                if (b >= 0) {
+                    m.add_count(b);
+#pragma unroll
+                    for (int a = 0; a < A_CT; ++a) m.add(a, b, vget<T>(a0[a], j));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < VN; ++j) {
+                int b = binner.bin(vget<T>(x1, j), vget<T>(y1, j));
+                if (b >= 0) {
+                    m.add_count(b);
+#pragma unroll
+                    for (int a = 0; a < A_CT; ++a) m.add(a, b, vget<T>(a1[a], j));
+                }
+            }
+        }
+        for (; gi < groups; gi += nthreads) {
+            V x0 = __ldcs(XV + gi), y0 = __ldcs(YV + gi);
+            V a0[AC];
+#pragma unroll
+            for (int a = 0; a < A_CT; ++a) a0[a] = __ldcs(AV[a] + gi);
+#pragma unroll
+            for (int j = 0; j < VN; ++j) {
+                int b = binner.bin(vget<T>(x0, j), vget<T>(y0, j));
+                if (b >= 0) {
+                    m.add_count(b);
+#pragma unroll
+                    for (int a = 0; a < A_CT; ++a) m.add(a, b, vget<T>(a0[a], j));
+                }
+            }
+        }
+    } else {
+        for (int64_t gi = tid; gi < groups; gi += nthreads) {
+            V x0 = __ldcs(XV + gi), y0 = __ldcs(YV + gi);
+#pragma unroll
+            for (int j = 0; j < VN; ++j) {
+                int b = binner.bin(vget<T>(x0, j), vget<T>(y0, j));
+                if (b < 0) continue;
+                m.add_count(b);
+                const int64_t i = head + gi * VN + j;
+                for (int a = 0; a < A; ++a) m.add(a, b, static_cast<const T*>(args.a[a])[i]);
+            }
+        }
+    }
+    __syncthreads();
+    m.merge(st, A);
+}
+
+// ------------------------------------------------------------------ host side
+template <typename T>
+static void vector_split(const BinArgs& a, int64_t* head, int64_t* groups) {
+    constexpr int VN = VecOf<T>::N;
+    auto phase = [](const void* p) { return (int)(((uintptr_t)p / sizeof(T)) % VN); };
+    const bool aligned = ((uintptr_t)a.x % sizeof(T)) == 0;
+    int ph = phase(a.x);
+    bool same = aligned && phase(a.y) == ph;
+    for (int k = 0; k < a.n_attrs; ++k) same = same && phase(a.a[k]) == ph;
+    if (!same) {
+        *head = a.n;
+        *groups = 0;
+        return;
+    }
+    int64_t h = (VN - ph) % VN;
+    if (h > a.n) h = a.n;
+    *head = h;
+    *groups = (a.n - h) / VN;
+}
+
+static size_t private_bytes_for(int dtype, int mode, int B, int A, bool s, bool lo, bool hi) {
+    const bool wide = dtype == BN_F64 || mode == kSumF64;
+    const size_t tsz = dtype == BN_F64 ? 8 : 4;
+    size_t b = ((size_t)B * 4 + 15) & ~(size_t)15;
+    if (s) b += (size_t)A * B * (wide ? 8 : (mode == kSumF32C ? 8 : 4));
+    if (lo) b += (size_t)A * B * tsz;
+    if (hi) b += (size_t)A * B * tsz;
+    return b;
+}
+
+size_t private_smem_bytes(const BinArgs& a, int smem_optin) {
+    const int64_t B = (int64_t)a.grid.ax[0].res * a.grid.ax[1].res;
+    if (B > (1 << 20)) return 0;
+    size_t b = private_bytes_for(a.dtype, a.dtype == BN_F64 ? kSumF64 : a.sum_mode, (int)B,
+                                 a.n_attrs, a.st.do_sum != 0, a.st.do_min != 0,
+                                 a.st.do_max != 0);
+    return b <= (size_t)smem_optin ? b : 0;
+}
+
+template <typename T, int A_CT, int MODE>
+static cudaError_t launch_private_t(const KernelCtx& kc, const BinArgs& a, size_t smem) {
+    auto kern = k_bin_private<T, A_CT, MODE>;
+    static bool configured = false;  // per instantiation
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kc.smem_optin);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int block = 512;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int64_t head, groups;
+    vector_split<T>(a, &head, &groups);
+    // enough particles per CTA to amortise clearing and merging its mesh
+    const int64_t B = (int64_t)a.grid.ax[0].res * a.grid.ax[1].res;
+    int64_t want = a.n / (4 * B > 16 * block ? 4 * B : 16 * block);
+    if (want < 1) want = 1;
+    int64_t grid = (int64_t)kc.num_sms * per_sm;
+    if (grid > want) grid = want;
+    kern<<<(int)grid, block, smem, kc.stream>>>(a, head, groups);
+    kc.count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+static cudaError_t dispatch_a(const KernelCtx& kc, const BinArgs& a, size_t smem) {
+    switch (a.n_attrs) {
+        case 1: return launch_private_t<T, 1, MODE>(kc, a, smem);
+        case 2: return launch_private_t<T, 2, MODE>(kc, a, smem);
+        case 3: return launch_private_t<T, 3, MODE>(kc, a, smem);
+        case 4: return launch_private_t<T, 4, MODE>(kc, a, smem);
+        default: return launch_private_t<T, -1, MODE>(kc, a, smem);
+    }
+}
+
+cudaError_t launch_bin_private(const KernelCtx& kc, const BinArgs& a) {
+    size_t smem = private_smem_bytes(a, kc.smem_optin);
+    if (smem == 0) return cudaErrorInvalidValue;
+    if (a.dtype == BN_F64) return dispatch_a<double, kSumF64>(kc, a, smem);
+    switch (a.sum_mode) {
+        case kSumF32: return dispatch_a<float, kSumF32>(kc, a, smem);
+        case kSumF64: return dispatch_a<float, kSumF64>(kc, a, smem);
+        default: return dispatch_a<float, kSumF32C>(kc, a, smem);
+    }
+}
+
+}  // namespace bn

@@ -1,0 +1,807 @@
+// runtime.cu -- the C ABI of libbinning.so (include/binning.h): contexts,
+// buffer handles, stream ordering, staging of host data, strategy choice and
+// request completion. Kernels live in k_*.cu; this file only plans and
+// queues them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "bn_internal.cuh"
+#include "bn_kernels.h"
+#include "bn_runtime.h"
+
+using namespace bn;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+bn_status bn::fail(bn_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+bn_status bn::cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? BN_ERR_NO_MEMORY : BN_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+extern "C" const char* bn_last_error(void) { return g_err.c_str(); }
+extern "C" const char* bn_version(void) { return "binning 0.1 (sm_103a)"; }
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+// ------------------------------------------------------------------ context
+namespace bn {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace bn
+
+static const int kStatusSlots = 4096;
+
+extern "C" bn_status bn_context_create(int device, const bn_options* opt, bn_context** out) {
+    if (!out) return fail(BN_ERR_INVALID_ARG, "bn_context_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev)
+        return fail(BN_ERR_INVALID_ARG, "bn_context_create: no CUDA device %d (%d present)", device, ndev);
+    DeviceGuard g(device);
+    auto* c = new (std::nothrow) bn_context();
+    if (!c) return fail(BN_ERR_NO_MEMORY, "bn_context_create: out of host memory");
+    c->device = device;
+    cudaDeviceProp p;
+    e = cudaGetDeviceProperties(&p, device);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDeviceProperties"); }
+    c->num_sms = p.multiProcessorCount;
+    c->profile = opt && (opt->flags & BN_CTX_PROFILE);
+    c->smem_optin = (int)p.sharedMemPerBlockOptin;
+    if (opt && opt->stream) {
+        c->stream = static_cast<cudaStream_t>(opt->stream);
+        c->own_stream = false;
+    } else {
+        int prio = opt ? opt->stream_priority : 0;
+        e = cudaStreamCreateWithPriority(&c->stream, cudaStreamNonBlocking, prio);
+        if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaStreamCreateWithPriority"); }
+        c->own_stream = true;
+    }
+    e = cudaDeviceGetDefaultMemPool(&c->pool, device);
+    if (e == cudaSuccess) {
+        uint64_t thr = (opt && opt->mempool_release_threshold) ? opt->mempool_release_threshold
+                                                                : UINT64_MAX;
+        cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    e = cudaHostAlloc(reinterpret_cast<void**>(&c->status_host), kStatusSlots * sizeof(int),
+                      cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return cuda_fail(e, "cudaHostAlloc(status)");
+    }
+    e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->status_dev), c->status_host, 0);
+    if (e != cudaSuccess) {
+        cudaFreeHost(c->status_host);
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return cuda_fail(e, "cudaHostGetDevicePointer(status)");
+    }
+    memset(c->status_host, 0, kStatusSlots * sizeof(int));
+    for (int i = kStatusSlots - 1; i >= 0; --i) c->free_slots.push_back(i);
+    *out = c;
+    return BN_OK;
+}
+
+extern "C" bn_status bn_context_destroy(bn_context* c) {
+    if (!c) return BN_OK;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t ev : c->event_pool) cudaEventDestroy(ev);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    cudaFreeHost(c->status_host);
+    delete c;
+    return BN_OK;
+}
+
+extern "C" bn_status bn_context_stream(bn_context* c, void** stream) {
+    if (!c || !stream) return fail(BN_ERR_INVALID_ARG, "bn_context_stream: NULL argument");
+    *stream = c->stream;
+    return BN_OK;
+}
+
+extern "C" bn_status bn_context_profile(bn_context* c, double* total_ms, uint64_t* n,
+                                        int32_t* last_strategy) {
+    if (!c || !total_ms || !n) return fail(BN_ERR_INVALID_ARG, "bn_context_profile: NULL argument");
+    if (last_strategy) *last_strategy = c->last_strategy;
+    DeviceGuard g(c->device);
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pairs;
+    {
+        std::lock_guard<std::mutex> lk(c->prof_mu);
+        pairs.swap(c->prof_pairs);
+    }
+    double tot = 0.0;
+    bn_status st = BN_OK;
+    for (auto& pr : pairs) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(pr.second);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+        if (e != cudaSuccess && st == BN_OK) st = cuda_fail(e, "bn_context_profile");
+        tot += ms;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    *total_ms = tot;
+    *n = pairs.size();
+    return st;
+}
+
+extern "C" bn_status bn_context_launch_count(bn_context* c, uint64_t* n) {
+    if (!c || !n) return fail(BN_ERR_INVALID_ARG, "bn_context_launch_count: NULL argument");
+    *n = c->launches.load();
+    return BN_OK;
+}
+
+cudaEvent_t bn_context::get_event() {
+    std::lock_guard<std::mutex> lk(pool_mu);
+    if (!event_pool.empty()) {
+        cudaEvent_t ev = event_pool.back();
+        event_pool.pop_back();
+        return ev;
+    }
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    return ev;
+}
+
+void bn_context::put_event(cudaEvent_t ev) {
+    if (!ev) return;
+    std::lock_guard<std::mutex> lk(pool_mu);
+    event_pool.push_back(ev);
+}
+
+int bn_context::get_slot() {
+    std::lock_guard<std::mutex> lk(pool_mu);
+    if (free_slots.empty()) return -1;
+    int s = free_slots.back();
+    free_slots.pop_back();
+    status_host[s] = 0;
+    return s;
+}
+
+void bn_context::put_slot(int s) {
+    if (s < 0) return;
+    std::lock_guard<std::mutex> lk(pool_mu);
+    free_slots.push_back(s);
+}
+
+// ------------------------------------------------------------------ requests
+bn_request* bn::new_request(bn_context* c) {
+    auto* r = new (std::nothrow) bn_request();
+    if (!r) return nullptr;
+    r->ctx = c;
+    r->slot = c->get_slot();
+    r->done = c->get_event();
+    if (r->slot < 0 || !r->done) {
+        c->put_slot(r->slot);
+        c->put_event(r->done);
+        delete r;
+        return nullptr;
+    }
+    return r;
+}
+
+static bn_status request_status_now(bn_request* r) {
+    if (r->host_status != BN_OK) return r->host_status;
+    if (r->external_done) {
+        int st = r->external_done->load(std::memory_order_acquire);
+        if (st == BN_NOT_READY) return BN_NOT_READY;
+        return (bn_status)st;
+    }
+    cudaError_t e = cudaEventQuery(r->done);
+    if (e == cudaErrorNotReady) return BN_NOT_READY;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventQuery");
+    int st = r->ctx->status_host[r->slot];
+    return (bn_status)st;
+}
+
+extern "C" bn_status bn_query(bn_request* r) {
+    if (!r) return fail(BN_ERR_INVALID_ARG, "bn_query: NULL request");
+    DeviceGuard g(r->ctx->device);
+    return request_status_now(r);
+}
+
+extern "C" bn_status bn_wait(bn_request* r, int64_t timeout_us) {
+    if (!r) return fail(BN_ERR_INVALID_ARG, "bn_wait: NULL request");
+    DeviceGuard g(r->ctx->device);
+    if (timeout_us < 0 && !r->external_done && r->host_status == BN_OK) {
+        cudaError_t e = cudaEventSynchronize(r->done);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        return request_status_now(r);
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    int64_t spin = 0;
+    for (;;) {
+        bn_status st = request_status_now(r);
+        if (st != BN_NOT_READY) return st;
+        auto el = std::chrono::duration_cast<std::chrono::microseconds>(
+                      std::chrono::steady_clock::now() - t0).count();
+        if (timeout_us >= 0 && el >= timeout_us)
+            return fail(BN_ERR_TIMEOUT, "bn_wait: request still running after %lld us",
+                        (long long)timeout_us);
+        if (++spin > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+void bn::run_deleters(bn_request* r) {
+    for (auto& d : r->deleters) d.fn(d.ptr, d.ctx);
+    r->deleters.clear();
+}
+
+extern "C" bn_status bn_request_release(bn_request* r) {
+    if (!r) return BN_OK;
+    DeviceGuard g(r->ctx->device);
+    if (r->external_done) {
+        while (r->external_done->load(std::memory_order_acquire) == BN_NOT_READY)
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+    } else if (r->host_status == BN_OK) {
+        cudaEventSynchronize(r->done);
+    }
+    run_deleters(r);
+    if (r->on_release) r->on_release(r);
+    r->ctx->put_event(r->done);
+    r->ctx->put_slot(r->slot);
+    delete r;
+    return BN_OK;
+}
+
+static void lib_free_deleter(void* ptr, void* ctx) {
+    (void)ctx;
+    if (ptr) cudaFree(ptr);  // memory from cudaMallocAsync may be freed with cudaFree
+}
+
+extern "C" bn_status bn_buffer_release(bn_buffer* b) {
+    if (!b) return BN_OK;
+    if (b->deleter) b->deleter(b->ptr, b->deleter_ctx);
+    memset(b, 0, sizeof *b);
+    return BN_OK;
+}
+
+// ------------------------------------------------------------------ planning
+static int dtype_size(int dt) { return dt == BN_F32 ? 4 : 8; }
+
+bn_status bn::validate_buffer(const bn_context* c, const bn_buffer* b, int64_t n, int dtype,
+                              const char* what) {
+    if (!b) return fail(BN_ERR_INVALID_ARG, "%s: NULL buffer", what);
+    if (b->n != n) return fail(BN_ERR_INVALID_ARG, "%s: length %lld, expected %lld", what,
+                               (long long)b->n, (long long)n);
+    if (b->dtype != dtype)
+        return fail(BN_ERR_INVALID_ARG, "%s: dtype %d, expected %d", what, b->dtype, dtype);
+    if (n > 0 && !b->ptr) return fail(BN_ERR_INVALID_ARG, "%s: NULL pointer", what);
+    if (b->stride < 0) return fail(BN_ERR_INVALID_ARG, "%s: negative stride", what);
+    if (b->device != BN_HOST && b->device != c->device)
+        return fail(BN_ERR_DEVICE_MISMATCH, "%s: buffer on device %d, context on device %d", what,
+                    b->device, c->device);
+    if (b->ptr && ((uintptr_t)b->ptr % (uintptr_t)dtype_size(dtype)) != 0)
+        return fail(BN_ERR_INVALID_ARG, "%s: pointer not aligned to its element size", what);
+    return BN_OK;
+}
+
+// Host-side mesh set-up for explicit bounds, in the coordinate type T:
+// lo_T = (T)lo, hi_T = (T)hi, s_T = (T)res / (hi_T - lo_T).
+template <typename T>
+static bn_status make_axis_host(double lo, double hi, int res, AxisDesc* d) {
+    if (!std::isfinite(lo) || !std::isfinite(hi))
+        return fail(BN_ERR_INVALID_ARG, "grid: bounds must be finite");
+    volatile T lo_t = (T)lo;
+    volatile T hi_t = (T)hi;
+    volatile T w = (T)(hi_t - lo_t);
+    if (!(w > (T)0) || !std::isfinite((double)w))
+        return fail(BN_ERR_INVALID_ARG, "grid: lo must be below hi (after rounding to the data type)");
+    volatile T s = (T)((T)res / w);
+    if (!(s > (T)0) || !std::isfinite((double)s))
+        return fail(BN_ERR_INVALID_ARG, "grid: res / (hi - lo) is not finite");
+    d->lo = (double)lo_t;
+    d->hi = (double)hi_t;
+    d->s = (double)s;
+    d->res = res;
+    d->closed = 0;
+    d->fast = 0;
+    d->pad = 0;
+    return BN_OK;
+}
+
+bn_status bn::make_grid_desc(const bn_grid* g, int dtype, GridDesc* out) {
+    if (!g) return fail(BN_ERR_INVALID_ARG, "grid: NULL");
+    for (int a = 0; a < 2; ++a)
+        if (g->res[a] < 1 || g->res[a] > BN_MAX_RES)
+            return fail(BN_ERR_INVALID_ARG, "grid: res[%d] = %d outside [1, %d]", a, g->res[a], BN_MAX_RES);
+    if ((int64_t)g->res[0] * g->res[1] > (int64_t)BN_MAX_BINS)
+        return fail(BN_ERR_INVALID_ARG, "grid: more than %d bins", BN_MAX_BINS);
+    memset(out, 0, sizeof *out);
+    out->valid = 1;
+    for (int a = 0; a < 2; ++a) {
+        out->ax[a].res = g->res[a];
+        if (g->auto_bounds) {
+            out->ax[a].closed = 1;
+            continue;
+        }
+        bn_status st = dtype == BN_F64 ? make_axis_host<double>(g->lo[a], g->hi[a], g->res[a], &out->ax[a])
+                                       : make_axis_host<float>(g->lo[a], g->hi[a], g->res[a], &out->ax[a]);
+        if (st != BN_OK) return st;
+    }
+    return BN_OK;
+}
+
+// Stream-ordered temporaries of one request.
+void* Plan::alloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, (bytes + 255) & ~(size_t)255, stream);
+    if (e != cudaSuccess) {
+        err = e;
+        return nullptr;
+    }
+    temps.push_back(p);
+    return p;
+}
+
+void Plan::free_temps() {
+    for (void* p : temps) cudaFreeAsync(p, stream);
+    temps.clear();
+}
+
+// Order the execution stream after work already queued on stream s.
+bn_status Plan::wait_on(void* s) {
+    cudaStream_t st = static_cast<cudaStream_t>(s);
+    if (st == stream) return BN_OK;
+    for (void* w : waited)
+        if (w == s) return BN_OK;
+    waited.push_back(s);
+    cudaEvent_t ev = ctx->get_event();
+    if (!ev) return fail(BN_ERR_CUDA, "cudaEventCreate failed");
+    cudaError_t e = cudaEventRecord(ev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev, 0);
+    ctx->put_event(ev);  // safe: a recorded event may be re-recorded later
+    if (e != cudaSuccess) return cuda_fail(e, "stream ordering");
+    return BN_OK;
+}
+
+// A device pointer with the column's data, contiguous: the buffer itself
+// (zero copy), or a staged copy (host data, or strided device data).
+bn_status Plan::column(const bn_buffer* b, int dtype, const void** out) {
+    const size_t es = dtype_size(dtype);
+    const int64_t n = b->n;
+    if (n == 0) {
+        *out = nullptr;
+        return BN_OK;
+    }
+    const int64_t stride = b->stride <= 1 ? 1 : b->stride;
+    if (b->device != BN_HOST) {
+        bn_status st = wait_on(b->stream);
+        if (st != BN_OK) return st;
+        if (stride == 1) {
+            *out = b->ptr;
+            return BN_OK;
+        }
+        void* t = alloc((size_t)n * es);
+        if (!t) return cuda_fail(err, "cudaMallocAsync(column)");
+        cudaError_t e = launch_gather(kc(), dtype, t, b->ptr, n, stride);
+        if (e != cudaSuccess) return cuda_fail(e, "gather kernel");
+        *out = t;
+        return BN_OK;
+    }
+    // host memory: the location-agnostic access of Sec. 2 (temporary + move)
+    void* t = alloc((size_t)n * es);
+    if (!t) return cuda_fail(err, "cudaMallocAsync(host column)");
+    cudaError_t e;
+    if (stride == 1)
+        e = cudaMemcpyAsync(t, b->ptr, (size_t)n * es, cudaMemcpyHostToDevice, stream);
+    else
+        e = cudaMemcpy2DAsync(t, es, b->ptr, (size_t)stride * es, es, (size_t)n,
+                              cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy host column");
+    h2d_bytes += (size_t)n * es;
+    *out = t;
+    return BN_OK;
+}
+
+// Device storage for one per-bin output: the caller's device buffer, a
+// library allocation handed back to the caller, or a temporary (host
+// outputs, or state the caller did not ask for). load: copy the caller's
+// host data in first (accumulate mode).
+bn_status Plan::output(bn_buffer* b, bool wanted, int64_t bins, int dtype, bool load, void** out) {
+    const size_t es = dtype_size(dtype);
+    if (wanted && b && b->ptr) {
+        if (b->n < bins) return fail(BN_ERR_INVALID_ARG, "output buffer holds %lld elements, mesh has %lld",
+                                     (long long)b->n, (long long)bins);
+        if (b->dtype != dtype) return fail(BN_ERR_INVALID_ARG, "output dtype %d, expected %d", b->dtype, dtype);
+        if (b->stride > 1) return fail(BN_ERR_INVALID_ARG, "output buffers must be contiguous");
+        if (b->device != BN_HOST && b->device != ctx->device)
+            return fail(BN_ERR_DEVICE_MISMATCH, "output on device %d, context on device %d", b->device, ctx->device);
+        if (((uintptr_t)b->ptr % es) != 0) return fail(BN_ERR_INVALID_ARG, "output pointer misaligned");
+        if (b->device != BN_HOST) {
+            bn_status st = wait_on(b->stream);
+            if (st != BN_OK) return st;
+            out_streams.push_back(b->stream);
+            *out = b->ptr;
+            return BN_OK;
+        }
+        void* t = alloc((size_t)bins * es);
+        if (!t) return cuda_fail(err, "cudaMallocAsync(output)");
+        if (load) {
+            cudaError_t e = cudaMemcpyAsync(t, b->ptr, (size_t)bins * es, cudaMemcpyHostToDevice, stream);
+            if (e != cudaSuccess) return cuda_fail(e, "copy host output in");
+            h2d_bytes += (size_t)bins * es;
+        }
+        d2h.push_back({b->ptr, t, (size_t)bins * es});
+        *out = t;
+        return BN_OK;
+    }
+    if (wanted && b && !b->ptr) {
+        if (load) return fail(BN_ERR_INVALID_ARG, "accumulate needs existing output buffers");
+        void* p = nullptr;
+        cudaError_t e = cudaMallocAsync(&p, (size_t)bins * es, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(library output)");
+        b->ptr = p;
+        b->n = bins;
+        b->stride = 1;
+        b->dtype = dtype;
+        b->device = ctx->device;
+        b->stream = stream;
+        b->alloc = BN_ALLOC_CUDA_ASYNC;
+        b->deleter = lib_free_deleter;
+        b->deleter_ctx = nullptr;
+        *out = p;
+        return BN_OK;
+    }
+    if (load) return fail(BN_ERR_INVALID_ARG, "accumulate needs count, sum, min and max outputs");
+    void* t = alloc((size_t)bins * es);
+    if (!t) return cuda_fail(err, "cudaMallocAsync(state)");
+    *out = t;
+    return BN_OK;
+}
+
+bn_status Plan::finish(bn_request* r) {
+    for (auto& c : d2h) {
+        cudaError_t e = cudaMemcpyAsync(c.host, c.dev, c.bytes, cudaMemcpyDeviceToHost, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy output to host");
+        d2h_bytes += c.bytes;
+    }
+    free_temps();
+    cudaError_t e = cudaEventRecord(r->done, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (void* s : out_streams) {
+        if (static_cast<cudaStream_t>(s) == stream) continue;
+        e = cudaStreamWaitEvent(static_cast<cudaStream_t>(s), r->done, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "order output stream");
+    }
+    return BN_OK;
+}
+
+// ------------------------------------------------------------------ binning
+int bn::choose_strategy(const BinArgs& a, int smem_optin, int num_sms, uint32_t ops) {
+    const uint32_t forced = ops & BN_STRATEGY_MASK;
+    if (forced == BN_STRATEGY_PRIVATE) return BN_STRATEGY_PRIVATE;
+    if (forced == BN_STRATEGY_GLOBAL) return BN_STRATEGY_GLOBAL;
+    if (forced == BN_STRATEGY_SORT) return BN_STRATEGY_SORT;
+    const size_t smem = private_smem_bytes(a, smem_optin);
+    const int64_t B = (int64_t)a.grid.ax[0].res * a.grid.ax[1].res;
+    // Privatise when the mesh fits and there are enough particles per CTA
+    // copy of the mesh to amortise clearing and merging it.
+    if (smem > 0 && a.n >= 2 * B) return BN_STRATEGY_PRIVATE;
+    (void)num_sms;
+    return BN_STRATEGY_GLOBAL;
+}
+
+bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const bn_buffer* y,
+                          const bn_buffer* attrs, int n_attrs, const bn_grid* grid, uint32_t ops,
+                          bn_result* out, int* status_dev) {
+    if (!x || !y || !grid || !out) return fail(BN_ERR_INVALID_ARG, "bn_bin_particles: NULL argument");
+    if (n_attrs < 0 || n_attrs > BN_MAX_ATTR)
+        return fail(BN_ERR_INVALID_ARG, "n_attrs = %d outside [0, %d]", n_attrs, BN_MAX_ATTR);
+    if (n_attrs > 0 && !attrs) return fail(BN_ERR_INVALID_ARG, "attrs is NULL");
+    const int dtype = x->dtype;
+    if (dtype != BN_F32 && dtype != BN_F64)
+        return fail(BN_ERR_INVALID_ARG, "coordinates must be BN_F32 or BN_F64");
+    const int64_t n = x->n;
+    if (n < 0) return fail(BN_ERR_INVALID_ARG, "negative length");
+    bn_status st = validate_buffer(c, x, n, dtype, "x");
+    if (st == BN_OK) st = validate_buffer(c, y, n, dtype, "y");
+    for (int a = 0; a < n_attrs && st == BN_OK; ++a) st = validate_buffer(c, &attrs[a], n, dtype, "attr");
+    if (st != BN_OK) return st;
+    if ((ops & BN_STRATEGY_MASK) > BN_STRATEGY_SORT)
+        return fail(BN_ERR_INVALID_ARG, "unknown strategy in ops");
+    const uint32_t sum_bits = ops & BN_SUM_MASK;
+    if (sum_bits == (3u << 8)) return fail(BN_ERR_INVALID_ARG, "unknown sum mode in ops");
+
+    GridDesc gd;
+    st = make_grid_desc(grid, dtype, &gd);
+    if (st != BN_OK) return st;
+    const int64_t B = (int64_t)grid->res[0] * grid->res[1];
+    const bool accumulate = (ops & BN_OP_ACCUMULATE) != 0;
+    const bool want_avg = (ops & BN_OP_AVG) != 0;
+    const bool want_sum = (ops & BN_OP_SUM) != 0;
+    const bool want_min = (ops & BN_OP_MIN) != 0;
+    const bool want_max = (ops & BN_OP_MAX) != 0;
+    const bool want_count = (ops & BN_OP_COUNT) != 0;
+    if (accumulate && (!want_count || (n_attrs > 0 && (!want_sum || !want_min || !want_max))))
+        return fail(BN_ERR_INVALID_ARG, "BN_OP_ACCUMULATE needs count, sum, min and max");
+    if (accumulate && grid->auto_bounds)
+        return fail(BN_ERR_INVALID_ARG, "BN_OP_ACCUMULATE needs explicit bounds");
+
+    BinArgs args;
+    memset(&args, 0, sizeof args);
+    args.dtype = dtype;
+    args.n_attrs = n_attrs;
+    args.sum_mode = dtype == BN_F64 ? kSumF64
+                    : sum_bits == BN_SUM_F32 ? kSumF32
+                    : sum_bits == BN_SUM_F64 ? kSumF64
+                                             : kSumF32C;
+    args.n = n;
+    st = plan.column(x, dtype, &args.x);
+    if (st == BN_OK) st = plan.column(y, dtype, &args.y);
+    for (int a = 0; a < n_attrs && st == BN_OK; ++a) st = plan.column(&attrs[a], dtype, &args.a[a]);
+    if (st != BN_OK) return st;
+
+    StateDesc& sd = args.st;
+    sd.bins = B;
+    sd.n_attrs = n_attrs;
+    sd.do_sum = (want_sum || want_avg) ? 1 : 0;
+    sd.do_min = want_min ? 1 : 0;
+    sd.do_max = want_max ? 1 : 0;
+    sd.do_avg = want_avg ? 1 : 0;
+    void* p = nullptr;
+    st = plan.output(&out->count, want_count, B, BN_U64, accumulate, &p);
+    if (st != BN_OK) return st;
+    sd.count = static_cast<unsigned long long*>(p);
+    for (int a = 0; a < n_attrs; ++a) {
+        if (sd.do_sum) {
+            st = plan.output(&out->sum[a], want_sum, B, BN_F64, accumulate, &p);
+            if (st != BN_OK) return st;
+            sd.sum[a] = static_cast<double*>(p);
+        }
+        if (want_min) {
+            st = plan.output(&out->min[a], true, B, dtype, accumulate, &p);
+            if (st != BN_OK) return st;
+            sd.mn[a] = p;
+        }
+        if (want_max) {
+            st = plan.output(&out->max[a], true, B, dtype, accumulate, &p);
+            if (st != BN_OK) return st;
+            sd.mx[a] = p;
+        }
+        if (want_avg) {
+            st = plan.output(&out->avg[a], true, B, BN_F64, false, &p);
+            if (st != BN_OK) return st;
+            sd.avg[a] = static_cast<double*>(p);
+        }
+    }
+    double* bounds_out = nullptr;
+    if (out->bounds.ptr) {
+        st = plan.output(&out->bounds, true, 4, BN_F64, false, &p);
+        if (st != BN_OK) return st;
+        bounds_out = static_cast<double*>(p);
+    }
+
+    const KernelCtx kc = plan.kc();
+    cudaError_t e;
+    void* bounds_acc = nullptr;
+    if (grid->auto_bounds) {
+        bounds_acc = plan.alloc(4 * dtype_size(dtype));
+        if (!bounds_acc) return cuda_fail(plan.err, "cudaMallocAsync(bounds)");
+    }
+    if (!accumulate || bounds_acc) {
+        StateDesc init = sd;
+        if (accumulate) init.bins = 0;  // keep the state, only reset bounds_acc
+        e = launch_init_state(kc, dtype, init, bounds_acc);
+        if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    }
+    GridDesc* dev_grid = nullptr;
+    if (dtype == BN_F64 || grid->auto_bounds || bounds_out) {
+        dev_grid = static_cast<GridDesc*>(plan.alloc(sizeof(GridDesc)));
+        long long* e0 = nullptr;
+        long long* e1 = nullptr;
+        if (dtype == BN_F64) {
+            e0 = static_cast<long long*>(plan.alloc(sizeof(long long) * (grid->res[0] + 1)));
+            e1 = static_cast<long long*>(plan.alloc(sizeof(long long) * (grid->res[1] + 1)));
+        }
+        if (!dev_grid || (dtype == BN_F64 && (!e0 || !e1))) return cuda_fail(plan.err, "cudaMallocAsync(grid)");
+        if (grid->auto_bounds && n > 0) {
+            e = launch_bounds_reduce(kc, dtype, args.x, args.y, n, bounds_acc);
+            if (e != cudaSuccess) return cuda_fail(e, "bounds kernel");
+        }
+        e = launch_grid_setup(kc, dtype, gd, bounds_acc, dev_grid, e0, e1, bounds_out, status_dev);
+        if (e != cudaSuccess) return cuda_fail(e, "grid set-up kernel");
+        args.dev_grid = dev_grid;
+    }
+    args.grid = gd;
+    if (n > 0) {
+        int strat = choose_strategy(args, c->smem_optin, c->num_sms, ops);
+        if (strat == BN_STRATEGY_SORT) strat = BN_STRATEGY_GLOBAL;
+        if (strat == BN_STRATEGY_PRIVATE && private_smem_bytes(args, c->smem_optin) == 0)
+            return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_PRIVATE: the mesh does not fit in shared memory");
+        plan.strategy = strat;
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        if (c->profile && cudaEventCreate(&t0) == cudaSuccess && cudaEventCreate(&t1) == cudaSuccess)
+            cudaEventRecord(t0, plan.stream);
+        e = strat == BN_STRATEGY_PRIVATE ? launch_bin_private(kc, args) : launch_bin_global(kc, args);
+        if (t1) {
+            cudaEventRecord(t1, plan.stream);
+            std::lock_guard<std::mutex> lk(c->prof_mu);
+            c->prof_pairs.emplace_back(t0, t1);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "binning kernel");
+    }
+    if (want_avg) {
+        e = launch_finalize(kc, sd);
+        if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
+    }
+    return BN_OK;
+}
+
+bn_status bn::complete_sync(bn_request* r, int sync, bn_request** req) {
+    if (sync) {
+        cudaError_t e = cudaEventSynchronize(r->done);
+        bn_status st = e == cudaSuccess ? request_status_now(r) : cuda_fail(e, "cudaEventSynchronize");
+        if (st == BN_NOT_READY) st = BN_OK;
+        if (req) {
+            *req = r;
+        } else {
+            bn_request_release(r);
+        }
+        if (st < 0 && bn_last_error()[0] == '\0') fail(st, "request failed on the device (status %d)", (int)st);
+        return st;
+    }
+    *req = r;
+    return BN_OK;
+}
+
+extern "C" bn_status bn_bin_particles(bn_context* c, const bn_buffer* x, const bn_buffer* y,
+                                      const bn_buffer* attrs, int n_attrs, const bn_grid* grid,
+                                      uint32_t ops, bn_result* out, int sync, bn_request** req) {
+    g_err.clear();
+    if (!c) return fail(BN_ERR_INVALID_ARG, "bn_bin_particles: NULL context");
+    if (!sync && !req) return fail(BN_ERR_INVALID_ARG, "bn_bin_particles: asynchronous call needs req");
+    if (req) *req = nullptr;
+    DeviceGuard g(c->device);
+    std::lock_guard<std::mutex> lk(c->enqueue_mu);
+    bn_request* r = new_request(c);
+    if (!r) return fail(BN_ERR_NO_MEMORY, "bn_bin_particles: no request slot");
+    Plan plan(c);
+    bn_status st = enqueue_bin(c, plan, x, y, attrs, n_attrs, grid, ops, out, c->status_dev + r->slot);
+    if (st == BN_OK) st = plan.finish(r);
+    if (st != BN_OK) {
+        std::string msg = g_err;
+        plan.free_temps();
+        cudaEventRecord(r->done, c->stream);
+        r->host_status = st;
+        bn_request_release(r);
+        g_err = msg;
+        return st;
+    }
+    if (x->deleter) r->deleters.push_back({x->deleter, x->ptr, x->deleter_ctx});
+    if (y->deleter) r->deleters.push_back({y->deleter, y->ptr, y->deleter_ctx});
+    for (int a = 0; a < n_attrs; ++a)
+        if (attrs[a].deleter) r->deleters.push_back({attrs[a].deleter, attrs[a].ptr, attrs[a].deleter_ctx});
+    if (plan.strategy) c->last_strategy = plan.strategy;
+    return complete_sync(r, sync, req);
+}
+
+// ------------------------------------------------------------------ merge
+extern "C" bn_status bn_merge_results(bn_context* c, const bn_result* parts, int n_parts,
+                                      int32_t dtype, int n_attrs, int64_t bins, uint32_t ops,
+                                      bn_result* out, int sync, bn_request** req) {
+    g_err.clear();
+    if (!c || !parts || !out) return fail(BN_ERR_INVALID_ARG, "bn_merge_results: NULL argument");
+    if (!sync && !req) return fail(BN_ERR_INVALID_ARG, "bn_merge_results: asynchronous call needs req");
+    if (n_parts < 1) return fail(BN_ERR_INVALID_ARG, "bn_merge_results: no parts");
+    if (dtype != BN_F32 && dtype != BN_F64) return fail(BN_ERR_INVALID_ARG, "bn_merge_results: bad dtype");
+    if (n_attrs < 0 || n_attrs > BN_MAX_ATTR) return fail(BN_ERR_INVALID_ARG, "bn_merge_results: bad n_attrs");
+    if (bins < 1 || bins > BN_MAX_BINS) return fail(BN_ERR_INVALID_ARG, "bn_merge_results: bad bins");
+    if (req) *req = nullptr;
+    DeviceGuard g(c->device);
+    std::lock_guard<std::mutex> lk(c->enqueue_mu);
+    bn_request* r = new_request(c);
+    if (!r) return fail(BN_ERR_NO_MEMORY, "bn_merge_results: no request slot");
+    Plan plan(c);
+    const bool want_avg = (ops & BN_OP_AVG) != 0;
+    bn_status st = BN_OK;
+    std::vector<StateDesc> hp((size_t)n_parts);
+    for (int p = 0; p < n_parts && st == BN_OK; ++p) {
+        StateDesc& s = hp[p];
+        memset(&s, 0, sizeof s);
+        s.bins = bins;
+        s.n_attrs = n_attrs;
+        auto dev_in = [&](const bn_buffer& b, int dt, void** outp) -> bn_status {
+            if (!b.ptr || b.n < bins || b.dtype != dt || b.device != c->device || b.stride > 1)
+                return fail(BN_ERR_INVALID_ARG, "bn_merge_results: part %d needs contiguous device count/sum/min/max of %lld bins", p, (long long)bins);
+            bn_status s2 = plan.wait_on(b.stream);
+            *outp = b.ptr;
+            return s2;
+        };
+        void* q = nullptr;
+        st = dev_in(parts[p].count, BN_U64, &q);
+        s.count = static_cast<unsigned long long*>(q);
+        for (int a = 0; a < n_attrs && st == BN_OK; ++a) {
+            st = dev_in(parts[p].sum[a], BN_F64, &q);
+            s.sum[a] = static_cast<double*>(q);
+            if (st == BN_OK) st = dev_in(parts[p].min[a], dtype, &s.mn[a]);
+            if (st == BN_OK) st = dev_in(parts[p].max[a], dtype, &s.mx[a]);
+        }
+    }
+    StateDesc sd;
+    memset(&sd, 0, sizeof sd);
+    sd.bins = bins;
+    sd.n_attrs = n_attrs;
+    sd.do_sum = 1;
+    sd.do_min = 1;
+    sd.do_max = 1;
+    sd.do_avg = want_avg;
+    void* q = nullptr;
+    if (st == BN_OK) st = plan.output(&out->count, true, bins, BN_U64, false, &q);
+    sd.count = static_cast<unsigned long long*>(q);
+    for (int a = 0; a < n_attrs && st == BN_OK; ++a) {
+        st = plan.output(&out->sum[a], true, bins, BN_F64, false, &q);
+        sd.sum[a] = static_cast<double*>(q);
+        if (st == BN_OK) st = plan.output(&out->min[a], true, bins, dtype, false, &sd.mn[a]);
+        if (st == BN_OK) st = plan.output(&out->max[a], true, bins, dtype, false, &sd.mx[a]);
+        if (st == BN_OK && want_avg) {
+            st = plan.output(&out->avg[a], true, bins, BN_F64, false, &q);
+            sd.avg[a] = static_cast<double*>(q);
+        }
+    }
+    StateDesc* dparts = nullptr;
+    if (st == BN_OK) {
+        dparts = static_cast<StateDesc*>(plan.alloc(sizeof(StateDesc) * n_parts));
+        if (!dparts) st = cuda_fail(plan.err, "cudaMallocAsync(parts)");
+    }
+    if (st == BN_OK) {
+        // pageable source: the copy completes before cudaMemcpyAsync returns
+        cudaError_t e = cudaMemcpyAsync(dparts, hp.data(), sizeof(StateDesc) * n_parts,
+                                        cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = launch_merge(c->kc(), dtype, sd, dparts, n_parts);
+        if (e == cudaSuccess && want_avg) e = launch_finalize(c->kc(), sd);
+        if (e != cudaSuccess) st = cuda_fail(e, "merge kernels");
+    }
+    if (st == BN_OK) st = plan.finish(r);
+    if (st != BN_OK) {
+        std::string msg = g_err;
+        plan.free_temps();
+        cudaEventRecord(r->done, c->stream);
+        r->host_status = st;
+        bn_request_release(r);
+        g_err = msg;
+        return st;
+    }
+    return complete_sync(r, sync, req);
+}

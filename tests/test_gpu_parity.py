@@ -1,0 +1,436 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Counts, bin indices, min and max bit-exact; FP64 sums within 1e-12 and
+FP32-compensated sums within 1e-6 of the per-bin sum of |a|. Sizes are
+chosen so the oracle finishes in seconds while the kernels still run many
+tiles with ragged tails; the slow tests run the full benchmark sizes.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from _parity import TOL_F32C, TOL_F64, abs_sums, assert_parity, run_gpu, to_numpy_result
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bn():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2310_02926_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(bn):
+    c = bn.Context(0)
+    yield c
+    c.close()
+
+
+def check(w, gpu, tol, auto_bounds=False, label=""):
+    ref = oracle.bin_workload(w, auto_bounds)
+    sabs = abs_sums(w, auto_bounds) if w.attrs else None
+    return assert_parity(gpu, ref, sabs, tol, label=label), ref
+
+
+# ------------------------------------------------------------------ configs
+@pytest.mark.parametrize("strategy", ["auto", "private", "global"])
+def test_uniform64_f64_config(bn, ctx, strategy):
+    """100,000 uniform particles, f64, 64x64 over [0,1)^2, all ops."""
+    w = workloads.uniform(100_000, seed=0, dtype=np.float64, res=64)
+    flags = {"auto": 0, "private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    check(w, run_gpu(ctx, w, flags=flags), TOL_F64, label=strategy)
+
+
+@pytest.mark.parametrize("strategy", ["auto", "global"])
+def test_plummer_f64_reduced(bn, ctx, strategy):
+    """Plummer sphere projected on x-y, 3 f64 attributes, 1024x1024 over [-10,10]^2."""
+    w = workloads.plummer(2_000_003, seed=1, dtype=np.float64, res=1024)
+    flags = {"auto": 0, "global": bn.STRATEGY_GLOBAL}[strategy]
+    check(w, run_gpu(ctx, w, flags=flags), TOL_F64, label=strategy)
+
+
+def test_private_rejects_mesh_too_large_for_shared_memory(bn, ctx):
+    w = workloads.plummer(10_000, seed=2, dtype=np.float64, res=1024)
+    with pytest.raises(bn.BinningError) as e:
+        run_gpu(ctx, w, flags=bn.STRATEGY_PRIVATE)
+    assert e.value.code == bn.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("res,strategy", [(1024, "global"), (64, "private"), (128, "global")])
+@pytest.mark.parametrize("mode", ["f32c", "f32", "f64"])
+def test_gaussians_f32_sum_modes(bn, ctx, res, strategy, mode):
+    """16-Gaussian mixture, f32 columns; the three sum modes against the FP64 oracle."""
+    w = workloads.gaussians(2 ** 21 + 13, seed=3, res=res)
+    flags = {"f32c": bn.SUM_F32C, "f32": bn.SUM_F32, "f64": bn.SUM_F64}[mode]
+    flags |= {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    gpu = run_gpu(ctx, w, flags=flags)
+    ref = oracle.bin_workload(w)
+    sabs = abs_sums(w)
+    if mode == "f32" and strategy == "private":
+        # plain FP32 partials: exact counts/min/max; sums bounded by the
+        # number of terms a CTA adds into one bin times 2^-24
+        assert_parity(gpu, ref, sabs, 1.0, label=mode)
+        rel = np.abs(gpu["sum"] - ref["sum"]) / np.where(sabs > 0, sabs, 1)
+        assert rel.max() < 1e-3
+    else:
+        tol = TOL_F64 if mode == "f64" or strategy == "global" else TOL_F32C
+        assert_parity(gpu, ref, sabs, tol, label=f"{mode}/{strategy}")
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("strategy", ["private", "global"])
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 31, 33, 1023, 1025, 70_001])
+def test_ragged_lengths(bn, ctx, dtype, strategy, n):
+    w = workloads.uniform(n, seed=4 + n, dtype=dtype, res=16)
+    flags = {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    check(w, run_gpu(ctx, w, flags=flags), TOL_F64 if dtype == np.float64 else TOL_F32C,
+          label=f"n={n}")
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("strategy", ["private", "global"])
+@pytest.mark.parametrize("offsets", [(1, 1, 1, 1), (1, 2, 3, 0), (3, 3, 3, 3)])
+def test_misaligned_columns(bn, ctx, dtype, strategy, offsets):
+    """Sub-range views whose starts are not 16-byte aligned (same or mixed phase)."""
+    w = workloads.uniform(50_000, seed=5, dtype=dtype, res=32)
+    dev = torch.device("cuda", 0)
+    n = w.n - 4
+    full = [torch.from_numpy(c).to(dev) for c in (w.x, w.y, *w.attrs)]
+    cols = [t[o:o + n] for t, o in zip(full, offsets)]
+    host = [np.ascontiguousarray(c[o:o + n]) for c, o in zip((w.x, w.y, *w.attrs), offsets)]
+    wv = workloads.Workload("view", host[0], host[1], host[2:], w.lo, w.hi, w.res)
+    flags = {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    out = ctx.bin_particles(cols[0], cols[1], cols[2:], w.lo, w.hi, w.res, ops=bn.OP_ALL | flags)
+    torch.cuda.synchronize()
+    check(wv, to_numpy_result(out), TOL_F64 if dtype == np.float64 else TOL_F32C)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_strided_columns(bn, ctx, dtype):
+    """Array-of-structs columns (element stride 4) are gathered, then binned."""
+    w = workloads.uniform(40_000, seed=6, dtype=dtype, res=24)
+    aos = np.stack([w.x, w.y, *w.attrs], axis=1)
+    t = torch.from_numpy(aos).to("cuda")
+    out = ctx.bin_particles(t[:, 0], t[:, 1], [t[:, 2], t[:, 3]], w.lo, w.hi, w.res)
+    torch.cuda.synchronize()
+    check(w, to_numpy_result(out), TOL_F64 if dtype == np.float64 else TOL_F32C)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("strategy", ["private", "global"])
+def test_special_values(bn, ctx, dtype, strategy):
+    rng = np.random.default_rng(7)
+    n = 20_000
+    x = rng.uniform(-0.2, 1.2, n).astype(dtype)
+    y = rng.uniform(-0.2, 1.2, n).astype(dtype)
+    a = rng.normal(0, 1, n).astype(dtype)
+    b = rng.uniform(-1, 1, n).astype(dtype)
+    x[::97] = np.nan
+    y[5::101] = np.inf
+    x[7::103] = -np.inf
+    x[11::89] = 0.0
+    x[13::89] = -0.0
+    y[17::83] = 1.0           # == hi: outside (half-open)
+    x[19::79] = np.nextafter(dtype(1.0), dtype(0.0))
+    a[::53] = np.nan
+    a[3::59] = -0.0
+    a[4::61] = 0.0
+    b[::67] = np.inf
+    b[1::71] = -np.inf
+    w = workloads.Workload("special", x, y, [a, b], (0.0, 0.0), (1.0, 1.0), (8, 8))
+    flags = {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    check(w, run_gpu(ctx, w, flags=flags), TOL_F64 if dtype == np.float64 else TOL_F32C)
+
+
+F64_GRIDS = [
+    ((-10.0, -10.0), (10.0, 10.0), (1024, 1024)),
+    ((-1.3, 0.1), (2.7, 0.35), (37, 5)),
+    ((0.0, 0.0), (1.0, 1.0), (3, 7)),
+    ((1e6, -3.0), (1e6 + 1.0, 3.0), (1000, 3)),    # too fine for the FP32 estimate
+    ((-1e-3, 5.0), (2e-3, 5.0 + 1e-9), (999, 17)),
+]
+
+
+@pytest.mark.parametrize("grid", F64_GRIDS)
+@pytest.mark.parametrize("strategy", ["private", "global"])
+def test_f64_bin_edges_exact(bn, ctx, grid, strategy):
+    """Particles on and within a few ulp of every bin edge: indices must
+    follow the round-to-nearest sequence exactly (via the edge-key method)."""
+    lo, hi, res = grid
+    if strategy == "private" and res[0] * res[1] * 4 * 8 > 200_000:
+        pytest.skip("mesh does not fit shared memory")
+    pts = []
+    for a in range(2):
+        s = res[a] / (hi[a] - lo[a])
+        for i in range(0, res[a] + 1, max(1, res[a] // 64)):
+            e = lo[a] + i / s
+            for k in range(-3, 4):
+                v = e
+                step = np.inf if k > 0 else -np.inf
+                for _ in range(abs(k)):
+                    v = np.nextafter(v, step)
+                pts.append((a, v))
+    rng = np.random.default_rng(8)
+    n = len(pts)
+    x = rng.uniform(lo[0], hi[0], n)
+    y = rng.uniform(lo[1], hi[1], n)
+    for k, (a, v) in enumerate(pts):
+        (x if a == 0 else y)[k] = v
+    m = rng.uniform(1, 2, n)
+    w = workloads.Workload("edges", x, y, [m], lo, hi, res)
+    flags = {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    check(w, run_gpu(ctx, w, flags=flags), TOL_F64)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("strategy", ["private", "global"])
+def test_auto_bounds(bn, ctx, dtype, strategy):
+    w = workloads.plummer(300_001, seed=9, dtype=dtype, res=40)
+    w.x[::1000] = np.nan
+    flags = {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    gpu = run_gpu(ctx, w, flags=flags, auto_bounds=True, bounds=True)
+    (_, ref) = check(w, gpu, TOL_F64 if dtype == np.float64 else TOL_F32C, auto_bounds=True)
+    assert gpu["bounds"].tolist() == ref["bounds"].tolist()
+
+
+def test_auto_bounds_degenerate_reports_error(bn, ctx):
+    x = torch.full((1000,), 3.0, dtype=torch.float64, device="cuda")
+    y = torch.linspace(0, 1, 1000, dtype=torch.float64, device="cuda")
+    with pytest.raises(bn.BinningError) as e:
+        ctx.bin_particles(x, y, [], res=(4, 4), auto_bounds=True)
+    assert e.value.code == bn.ERR_DEGENERATE
+    out, req = ctx.bin_particles(x, y, [], res=(4, 4), auto_bounds=True, sync=False)
+    with pytest.raises(bn.BinningError) as e:
+        bn.bn_wait(req, 5_000_000)
+    assert e.value.code == bn.ERR_DEGENERATE
+    bn.bn_request_release(req)
+    # the context stays usable
+    w = workloads.uniform(1000, seed=10, res=4)
+    check(w, run_gpu(ctx, w), TOL_F64)
+
+
+# ------------------------------------------------------------------ data model
+def test_host_inputs_and_outputs(bn, ctx):
+    """Location-agnostic access: host columns are staged to the device, host
+    outputs are copied back."""
+    w = workloads.uniform(123_457, seed=11, dtype=np.float64, res=32)
+    cols = [torch.from_numpy(c) for c in (w.x, w.y, *w.attrs)]
+    out = bn.alloc_outputs(2, 32 * 32, torch.float64, torch.device("cpu"))
+    ctx.bin_particles(cols[0], cols[1], cols[2:], w.lo, w.hi, w.res, out=out)
+    check(w, to_numpy_result(out), TOL_F64)
+    pinned = [c.pin_memory() for c in cols]
+    out2 = bn.alloc_outputs(2, 32 * 32, torch.float64, torch.device("cpu"))
+    ctx.bin_particles(pinned[0], pinned[1], pinned[2:], w.lo, w.hi, w.res, out=out2)
+    check(w, to_numpy_result(out2), TOL_F64)
+
+
+def test_library_allocated_outputs(bn, ctx):
+    w = workloads.uniform(50_000, seed=12, dtype=np.float32, res=20)
+    cols = [torch.from_numpy(c).cuda() for c in (w.x, w.y, *w.attrs)]
+    r = bn.bn_result()  # every handle zeroed: the library allocates
+    bn.bn_bin_particles(ctx.handle, cols[0], cols[1], cols[2:], bn.grid(w.lo, w.hi, w.res),
+                        bn.OP_ALL, r, True)
+    B = 400
+    assert r.count.ptr and r.count.alloc == bn.ALLOC_CUDA_ASYNC and r.count.n == B
+
+    cudart = ctypes.CDLL("libcudart.so.13")
+
+    def fetch(buf, dt):
+        tdt = {np.uint64: torch.int64, np.float64: torch.float64, np.float32: torch.float32}[dt]
+        t = torch.empty(B, dtype=tdt, device="cuda")
+        torch.cuda.synchronize()
+        rc = cudart.cudaMemcpy(ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(buf.ptr),
+                               ctypes.c_size_t(B * t.element_size()), 3)  # device to device
+        assert rc == 0
+        return t.cpu().numpy().view(dt)
+
+    gpu = {"count": fetch(r.count, np.uint64),
+           "sum": np.stack([fetch(r.sum[a], np.float64) for a in range(2)]),
+           "min": np.stack([fetch(r.min[a], np.float32) for a in range(2)]),
+           "max": np.stack([fetch(r.max[a], np.float32) for a in range(2)]),
+           "avg": np.stack([fetch(r.avg[a], np.float64) for a in range(2)])}
+    check(w, gpu, TOL_F32C)
+    bn.lib().bn_buffer_release(ctypes.byref(r.count))
+    assert not r.count.ptr
+    for a in range(2):
+        for key in ("sum", "min", "max", "avg"):
+            bn.lib().bn_buffer_release(ctypes.byref(getattr(r, key)[a]))
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_accumulate_shards_into_one_state(bn, ctx, dtype):
+    w = workloads.plummer(400_000, seed=13, dtype=dtype, res=128)
+    cols = [torch.from_numpy(c).cuda() for c in (w.x, w.y, *w.attrs)]
+    out = bn.alloc_outputs(3, 128 * 128, cols[0].dtype, torch.device("cuda"))
+    cuts = [0, 1, 150_000, 150_003, w.n]
+    for k, (a, b) in enumerate(zip(cuts[:-1], cuts[1:])):
+        ops = bn.OP_ALL | (bn.OP_ACCUMULATE if k else 0)
+        ctx.bin_particles(cols[0][a:b], cols[1][a:b], [c[a:b] for c in cols[2:]], w.lo, w.hi,
+                          w.res, ops=ops, out=out)
+    torch.cuda.synchronize()
+    check(w, to_numpy_result(out), TOL_F64 if dtype == np.float64 else TOL_F32C)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_merge_partial_results(bn, ctx, dtype):
+    """Shard, bin each shard, merge the partial meshes (the per-rank merge)."""
+    w = workloads.plummer(300_000, seed=14, dtype=dtype, res=64)
+    cols = [torch.from_numpy(c).cuda() for c in (w.x, w.y, *w.attrs)]
+    B = 64 * 64
+    parts, structs = [], []
+    for a, b in ((0, 100_000), (100_000, 100_001), (100_001, w.n)):
+        o = ctx.bin_particles(cols[0][a:b], cols[1][a:b], [c[a:b] for c in cols[2:]], w.lo,
+                              w.hi, w.res)
+        parts.append(o)
+        structs.append(bn.result_struct(o))
+    merged = bn.alloc_outputs(3, B, cols[0].dtype, torch.device("cuda"))
+    bn.bn_merge_results(ctx.handle, structs, bn.F64 if dtype == np.float64 else bn.F32, 3, B,
+                        bn.OP_ALL, bn.result_struct(merged), True)
+    check(w, to_numpy_result(merged), TOL_F64 if dtype == np.float64 else TOL_F32C)
+
+
+def test_batch_of_uneven_blocks(bn, ctx):
+    plan = workloads.batch(n_blocks=12, seed=15, size_range=(1e3, 2e5), side_range=(8, 600))
+    blocks, outs, keep = [], [], []
+    for k in range(plan.n_blocks):
+        w = plan.block(k)
+        cols = [torch.from_numpy(c).cuda() for c in (w.x, w.y, *w.attrs)]
+        o = bn.alloc_outputs(2, w.res[0] * w.res[1], torch.float32, torch.device("cuda"))
+        r = bn.result_struct(o)
+        keep += [cols, r]
+        outs.append((w, o))
+        blocks.append(bn.block(cols[0], cols[1], cols[2:], bn.grid(w.lo, w.hi, w.res), r))
+    bn.bn_bin_batch(ctx.handle, blocks, bn.OP_ALL)
+    torch.cuda.synchronize()
+    for w, o in outs:
+        check(w, to_numpy_result(o), TOL_F32C, label=w.name)
+
+
+def test_async_query_and_wait(bn, ctx):
+    w = workloads.uniform(2_000_000, seed=16, dtype=np.float64, res=64)
+    cols = [torch.from_numpy(c).cuda() for c in (w.x, w.y, *w.attrs)]
+    out, req = ctx.bin_particles(cols[0], cols[1], cols[2:], w.lo, w.hi, w.res, sync=False)
+    st = bn.bn_query(req)
+    assert st in (bn.OK, bn.NOT_READY)
+    assert bn.bn_wait(req, 10_000_000) == bn.OK
+    assert bn.bn_query(req) == bn.OK
+    bn.bn_request_release(req)
+    check(w, to_numpy_result(out), TOL_F64)
+
+
+@pytest.mark.parametrize("ops_name", ["count", "count_avg", "min", "sum_max"])
+def test_op_subsets(bn, ctx, ops_name):
+    ops = {"count": bn.OP_COUNT, "count_avg": bn.OP_COUNT | bn.OP_AVG, "min": bn.OP_MIN,
+           "sum_max": bn.OP_SUM | bn.OP_MAX}[ops_name]
+    w = workloads.plummer(100_000, seed=17, dtype=np.float64, res=50)
+    gpu = run_gpu(ctx, w, ops=ops)
+    ref = oracle.bin_workload(w)
+    if "count" not in gpu:
+        gpu["count"] = ref["count"]
+    assert_parity(gpu, ref, abs_sums(w), TOL_F64, check=tuple(k for k in gpu))
+
+
+def test_invalid_arguments_are_reported(bn, ctx):
+    x = torch.zeros(10, dtype=torch.float64, device="cuda")
+    y = torch.zeros(11, dtype=torch.float64, device="cuda")
+    with pytest.raises(bn.BinningError) as e:
+        ctx.bin_particles(x, y, [])
+    assert e.value.code == bn.ERR_INVALID_ARG
+    y = torch.zeros(10, dtype=torch.float32, device="cuda")
+    with pytest.raises(bn.BinningError):
+        ctx.bin_particles(x, y, [])
+    y = torch.zeros(10, dtype=torch.float64, device="cuda")
+    for lo, hi, res in [((0, 0), (1, 1), (0, 4)), ((1, 0), (1, 1), (4, 4)),
+                        ((0, 0), (1, 1), (70_000, 1)), ((0, 0), (math.inf, 1), (4, 4))]:
+        with pytest.raises(bn.BinningError) as e:
+            ctx.bin_particles(x, y, [], lo, hi, res)
+        assert e.value.code == bn.ERR_INVALID_ARG
+    many = (bn.bn_buffer * 17)(*[bn.buffer(x) for _ in range(17)])
+    r = bn.bn_result()
+    st = bn.lib().bn_bin_particles(ctx.handle, ctypes.byref(bn.buffer(x)), ctypes.byref(bn.buffer(y)),
+                                   many, 17, ctypes.byref(bn.grid()), bn.OP_COUNT, ctypes.byref(r),
+                                   1, None)
+    assert st == bn.ERR_INVALID_ARG
+    bx = bn.buffer(x)
+    bx.device = 7
+    by = bn.buffer(y)
+    r = bn.bn_result()
+    st = bn.lib().bn_bin_particles(ctx.handle, ctypes.byref(bx), ctypes.byref(by), None, 0,
+                                   ctypes.byref(bn.grid()), bn.OP_COUNT, ctypes.byref(r), 1, None)
+    assert st == bn.ERR_DEVICE_MISMATCH
+    assert b"device" in bn.lib().bn_last_error()
+
+
+# ------------------------------------------------------------------ serving
+def test_server_results_equal_alone(bn, ctx):
+    """Requests binned in the server's batches give the same result as alone."""
+    plan = workloads.serving(n_requests=24, seed=18, size_range=(1e3, 3e5), side_range=(16, 300),
+                             pool_n=400_000)
+    pool = [torch.from_numpy(c).cuda() for c in (plan.pool.x, plan.pool.y, *plan.pool.attrs)]
+    srv = bn.bn_server_create(ctx.handle, 1 << 28, max_inflight=3, max_batch=5)
+    reqs = []
+    for i in range(plan.n_requests):
+        o0, n = int(plan.offsets[i]), int(plan.sizes[i])
+        side = int(plan.sides[i])
+        cols = [c[o0:o0 + n] for c in pool]
+        o = bn.alloc_outputs(3, side * side, torch.float32, torch.device("cuda"))
+        r = bn.result_struct(o)
+        blk = bn.block(cols[0], cols[1], cols[2:], bn.grid((-10, -10), (10, 10), (side, side)), r)
+        reqs.append((bn.bn_server_submit(srv, blk, bn.OP_ALL), o, r, blk, (o0, n, side)))
+    for req, o, r, blk, (o0, n, side) in reqs:
+        assert bn.bn_wait(req, 60_000_000) == bn.OK
+        bn.bn_request_release(req)
+    stats = bn.bn_server_stats_get(srv)
+    bn.bn_server_destroy(srv)
+    assert stats["completed"] == plan.n_requests and stats["failed"] == 0
+    for req, o, r, blk, (o0, n, side) in reqs:
+        alone = ctx.bin_particles(*[c[o0:o0 + n] for c in pool[:2]],
+                                  [c[o0:o0 + n] for c in pool[2:]], (-10, -10), (10, 10), (side, side))
+        torch.cuda.synchronize()
+        g, a = to_numpy_result(o), to_numpy_result(alone)
+        np.testing.assert_array_equal(g["count"], a["count"])
+        np.testing.assert_array_equal(g["min"], a["min"])
+        np.testing.assert_array_equal(g["max"], a["max"])
+        w = workloads.Workload("req", plan.pool.x[o0:o0 + n], plan.pool.y[o0:o0 + n],
+                               [c[o0:o0 + n] for c in plan.pool.attrs], (-10, -10), (10, 10),
+                               (side, side))
+        check(w, g, TOL_F32C)
+
+
+def test_server_rejects_over_budget(bn, ctx):
+    x = torch.zeros(1 << 20, dtype=torch.float32, device="cuda")
+    o = bn.alloc_outputs(0, 16, torch.float32, torch.device("cuda"), ops=bn.OP_COUNT)
+    r = bn.result_struct(o)
+    srv = bn.bn_server_create(ctx.handle, 1 << 20)
+    blk = bn.block(x, x, [], bn.grid(res=(4, 4)), r)
+    with pytest.raises(bn.BinningError) as e:
+        bn.bn_server_submit(srv, blk, bn.OP_COUNT)
+    assert e.value.code == bn.ERR_BUDGET
+    bn.bn_server_destroy(srv)
+
+
+# ------------------------------------------------------------------ full size
+@pytest.mark.slow
+def test_plummer_f64_full_size(bn, ctx):
+    """50,000,000 Plummer particles, f64, 3 attributes, 1024x1024: the
+    benchmark workload, in the launch configuration the benchmark times."""
+    w = workloads.plummer(50_000_000, seed=0, dtype=np.float64, res=1024)
+    check(w, run_gpu(ctx, w), TOL_F64, label="plummer full")
+
+
+@pytest.mark.slow
+def test_gaussians_f32_full_size(bn, ctx):
+    """2^27 f32 particles from 16 Gaussians on a 4096x4096 mesh (compensated sums)."""
+    w = workloads.gaussians(2 ** 27, seed=0, res=4096)
+    check(w, run_gpu(ctx, w), TOL_F32C, label="gaussians full")
