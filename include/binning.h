@@ -276,6 +276,38 @@ BN_API bn_status bn_bin_particles(bn_context* ctx, const bn_buffer* x, const bn_
                            uint32_t ops, bn_result* out, int sync, bn_request** req);
 
 /*
+ * bn_bin_particles without any allocation (the paper has no counterpart:
+ * this is for callers that cannot allocate). A simulation that has given all
+ * device memory to its own pool, code that must not call cudaMalloc (it can
+ * synchronise the device or fail at that point), or a process that must keep
+ * its memory footprint fixed after start-up can still bin with this call:
+ * it allocates no device or host memory, creates no stream or event and needs
+ * no bn_context. Its only scratch (mesh descriptor, automatic-bounds
+ * accumulator, a status word, the f64 bin-edge keys) is one fixed 64 KiB
+ * array that every GPU loading the library holds until the process exits.
+ *   x, y, attrs, out  device buffers of the current CUDA device, contiguous;
+ *                     count must be given, and sum[a] whenever avg is asked
+ *                     for (they hold the running state); other outputs as
+ *                     selected by ops. Buffer streams are ignored.
+ *   ops               BN_OP_* and BN_SUM_* bits; no accumulate or strategy bits
+ *   stream            all work is queued here (NULL = legacy default stream)
+ *   sync              1: wait and return the device status (e.g.
+ *                     BN_ERR_DEGENERATE); 0: return after queueing, device
+ *                     errors are then not reported
+ * Limit: f64 meshes need res_x + res_y <= 8062 (the edge keys must fit the
+ * array); larger meshes are rejected with BN_ERR_INVALID_ARG. f32 meshes
+ * have the usual limits.
+ * The first call on each device looks up the array's device address; make
+ * that first call before any stream capture. Calls share the array and it
+ * keeps the last call's contents (each call rewrites what it reads); calls
+ * whose work overlaps on the GPU race on it and must be serialised.
+ */
+BN_API bn_status bn_bin_particles_static(const bn_buffer* x, const bn_buffer* y,
+                                         const bn_buffer* attrs, int n_attrs,
+                                         const bn_grid* grid, uint32_t ops,
+                                         const bn_result* out, void* stream, int sync);
+
+/*
  * Bin many independent blocks, each with its own columns, mesh and outputs,
  * in one persistent launch (the many binning operations per in situ step of
  * Sec. 4.3). Every block follows the rules of bn_bin_particles; all blocks

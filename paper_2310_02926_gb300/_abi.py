@@ -112,6 +112,10 @@ PROTOTYPES = {
     "bn_bin_particles": (S, [P, ctypes.POINTER(bn_buffer), ctypes.POINTER(bn_buffer),
                              ctypes.POINTER(bn_buffer), ctypes.c_int, ctypes.POINTER(bn_grid),
                              ctypes.c_uint32, ctypes.POINTER(bn_result), ctypes.c_int, PP]),
+    "bn_bin_particles_static": (S, [ctypes.POINTER(bn_buffer), ctypes.POINTER(bn_buffer),
+                                    ctypes.POINTER(bn_buffer), ctypes.c_int,
+                                    ctypes.POINTER(bn_grid), ctypes.c_uint32,
+                                    ctypes.POINTER(bn_result), P, ctypes.c_int]),
     "bn_bin_batch": (S, [P, ctypes.POINTER(bn_block), ctypes.c_int, ctypes.c_uint32,
                          ctypes.c_int, PP]),
     "bn_merge_results": (S, [P, ctypes.POINTER(bn_result), ctypes.c_int, ctypes.c_int32,
