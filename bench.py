@@ -41,8 +41,29 @@ UNIT = "particles/s"
 N_PART = 50_000_000
 RES = 1024
 N_ATTR = 3
-KERNEL_SOURCES = ["paper_2310_02926_gb300/csrc/k_global.cu",
-                  "paper_2310_02926_gb300/csrc/bn_internal.cuh"]
+
+# name -> (generator, default particles, mesh side, attributes, dtype label, description)
+WORKLOADS = {
+    "plummer1024": ("plummer", 50_000_000, 1024, 3, "f64",
+                    "plummer a=1 r<10 x-y, {n:,} particles, 3 f64 attributes, 1024x1024 mesh over "
+                    "[-10,10]^2, count/sum/min/max/avg"),
+    "uniform64": ("uniform", 100_000, 64, 2, "f64",
+                  "uniform [0,1)^2, {n:,} particles, f64 mass U[1,2] and speed |N(0,1)|, 64x64 mesh, "
+                  "count/sum/min/max/avg"),
+    "uniform64_at_scale": ("uniform", 2 ** 27, 64, 2, "f64",
+                           "uniform [0,1)^2, {n:,} particles, f64 mass U[1,2] and speed |N(0,1)|, "
+                           "64x64 mesh, count/sum/min/max/avg"),
+    "gaussians4096": ("gaussians", 2 ** 27, 4096, 2, "f32",
+                      "16-Gaussian mixture in [0,1)^2, {n:,} f32 particles, 2 f32 attributes "
+                      "U[0,1e4], 4096x4096 mesh, count/sum/min/max/avg"),
+}
+# kernel sources whose ncu traffic record applies, per particle-pass strategy
+KERNEL_SOURCES = {
+    "global": ["paper_2310_02926_gb300/csrc/k_global.cu"],
+    "private": ["paper_2310_02926_gb300/csrc/k_private.cu", "paper_2310_02926_gb300/csrc/bn_device.cuh"],
+    "sort": ["paper_2310_02926_gb300/csrc/k_sort.cu", "paper_2310_02926_gb300/csrc/bn_device.cuh"],
+}
+COMMON_SOURCES = ["paper_2310_02926_gb300/csrc/bn_internal.cuh"]
 
 
 def peaks():
@@ -54,23 +75,26 @@ def peaks():
         return 6800.0, "fallback 6.8 TB/s"
 
 
-def kernel_source_sha() -> str:
+def kernel_source_sha(strategy: str) -> str:
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in KERNEL_SOURCES.get(strategy, []) + COMMON_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes per launch of the particle-pass kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
+def ncu_traffic(workload: str, strategy: str, n: int):
+    """DRAM bytes per launch of the particle pass from the committed ncu
+    record for this workload and strategy, if it was taken on the current
+    kernel source and at this size."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            t = json.load(f)
-        if t.get("source_sha") == kernel_source_sha():
-            return t.get("dram_bytes_per_launch_full"), t.get("note")
+            recs = json.load(f)
+        for t in recs if isinstance(recs, list) else [recs]:
+            if (t.get("workload") == workload and t.get("strategy") == strategy
+                    and t.get("full_n") == n and t.get("source_sha") == kernel_source_sha(strategy)):
+                return t.get("dram_bytes_per_launch_full"), t.get("note")
     except Exception:
         pass
     return None, None
@@ -143,11 +167,21 @@ def dist_env():
     return rank, world, local
 
 
-def workload_config(dtype="f64"):
-    return {"workload": f"plummer a=1 r<10 x-y, {N_PART:,} particles, {N_ATTR} {dtype} "
-                        f"attributes, {RES}x{RES} mesh over [-10,10]^2, count/sum/min/max/avg",
-            "n_particles": N_PART, "grid": [RES, RES], "n_attrs": N_ATTR, "dtype": dtype,
-            "l2": "inputs 2.0 GB > 129 MB L2: no flush between steps"}
+def make_workload(name: str, n: int, seed: int):
+    import numpy as np
+    import workloads
+    gen, _, side, _, dt, _ = WORKLOADS[name]
+    dtype = np.float64 if dt == "f64" else np.float32
+    return getattr(workloads, gen)(n, seed=seed, dtype=dtype, res=side)
+
+
+def workload_config(name: str, n: int, input_bytes: int):
+    gen, _, side, n_attrs, dt, desc = WORKLOADS[name]
+    l2 = (f"inputs {input_bytes / 1e9:.2f} GB > 129 MB L2: no flush between steps"
+          if input_bytes > 129e6 else
+          f"inputs {input_bytes / 1e6:.1f} MB fit in L2: L2-resident latency case, not an HBM figure")
+    return {"workload": desc.format(n=n), "name": name, "n_particles": n, "grid": [side, side],
+            "n_attrs": n_attrs, "dtype": dt, "l2": l2}
 
 
 def time_oracle(w, min_seconds: float, max_reps: int):
@@ -169,8 +203,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     import workloads
-    sample_n = args.reference_sample
-    w = workloads.plummer(sample_n, seed=0, dtype="float64", res=RES)
+    sample_n = min(args.reference_sample, WORKLOADS[args.workload][1])
+    w = make_workload(args.workload, sample_n, seed=0)
     import oracle
     oracle.build()
     for _ in range(max(0, min(args.warmup, 1))):
@@ -185,8 +219,9 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": workload_config(),
+            "scaling": "weak", "vs_baseline": None, "dtype": WORKLOADS[args.workload][4],
+            "data": "synthetic", "impl": "reference",
+            "config": workload_config(args.workload, WORKLOADS[args.workload][1], w.bytes_read()),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{sample_n:,} particles of the same workload per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -206,14 +241,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-sample", type=int, default=2_000_000)
     ap.add_argument("--strategy", default="auto", choices=["auto", "global", "private", "sort"])
-    ap.add_argument("--n", type=int, default=50_000_000,
-                    help="particles (smaller cases for profiling runs; the bench line uses the default)")
+    ap.add_argument("--workload", default="plummer1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=0,
+                    help="particles (0 = the workload's size; smaller cases for profiling runs)")
+    ap.add_argument("--sum", default="f32c", choices=["f32c", "f32", "f64"],
+                    help="sum mode for f32 workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
-    N_PART = args.n
+    N_PART = args.n or WORKLOADS[args.workload][1]
 
     import numpy as np
     import torch
@@ -232,18 +270,22 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
 
-    w = workloads.plummer(N_PART, seed=rank, dtype=np.float64, res=RES)
+    w = make_workload(args.workload, N_PART, seed=rank)
+    RES = w.res[0]
+    N_ATTR = len(w.attrs)
     B = RES * RES
+    tdtype = torch.float64 if w.x.dtype == np.float64 else torch.float32
+    dt_label = WORKLOADS[args.workload][4]
     stream = torch.cuda.Stream(device=dev)
     cols = [torch.from_numpy(c).to(dev) for c in (w.x, w.y, *w.attrs)]
     ctx = bn.Context(local, stream=stream.cuda_stream, profile=True)
     flags = {"auto": 0, "global": bn.STRATEGY_GLOBAL, "private": bn.STRATEGY_PRIVATE,
              "sort": bn.STRATEGY_SORT}[args.strategy]
-    ops = bn.OP_ALL | flags
+    ops = bn.OP_ALL | flags | {"f32c": bn.SUM_F32C, "f32": bn.SUM_F32, "f64": bn.SUM_F64}[args.sum]
     g = bn.grid(w.lo, w.hi, w.res)
     torch.cuda.synchronize(dev)
     with torch.cuda.stream(stream):
-        out = bn.alloc_outputs(N_ATTR, B, torch.float64, dev)
+        out = bn.alloc_outputs(N_ATTR, B, tdtype, dev)
         res_struct = bn.result_struct(out)
 
         def step():
@@ -284,20 +326,21 @@ def main():
 
     value = N_PART * args.steps * world / (elapsed_ms / 1e3)
     bytes_in = w.bytes_read()
-    bytes_state = B * (8 + N_ATTR * (8 + 2 * 8))   # count, sum, min, max
+    tsz = w.x.dtype.itemsize
+    bytes_state = B * (8 + N_ATTR * (8 + 2 * tsz))   # count, sum, min, max
     bytes_out = w.bytes_written()                    # + avg
     hbm, peak_src = peaks()
     step_gbs = (bytes_in + bytes_out) / (elapsed_ms / args.steps / 1e3) / 1e9
     kern_avg_ms = kern_ms / max(1, kern_launches)
     kern_bytes = bytes_in + bytes_state
     achieved = kern_bytes / (kern_avg_ms / 1e3) / 1e9 if kern_launches else None
-    traffic, traffic_note = ncu_traffic()
+    traffic, traffic_note = ncu_traffic(args.workload, strategy, N_PART)
 
     # end to end through the public API with pinned host buffers
     e2e = None
     if args.e2e_steps > 0 and rank == 0:
         hcols = [torch.from_numpy(c).pin_memory() for c in (w.x, w.y, *w.attrs)]
-        hout = bn.alloc_outputs(N_ATTR, B, torch.float64, torch.device("cpu"))
+        hout = bn.alloc_outputs(N_ATTR, B, tdtype, torch.device("cpu"))
         for k in ("count",):
             hout[k] = hout[k].pin_memory()
         for k in ("sum", "min", "max", "avg"):
@@ -322,8 +365,9 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(), strategy=strategy,
+            "scaling": "weak", "vs_baseline": None, "dtype": dt_label, "data": "synthetic",
+            "config": dict(workload_config(args.workload, N_PART, bytes_in), strategy=strategy,
+                           sum_mode=args.sum if dt_label == "f32" else "f64",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
             "hbm_frac_step": step_gbs / hbm,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

@@ -170,7 +170,15 @@ enum {
     BN_STRATEGY_PRIVATE = 1u << 12, /* per-CTA shared-memory copy of the mesh */
     BN_STRATEGY_GLOBAL = 2u << 12,  /* warp-aggregated atomics into the global mesh */
     BN_STRATEGY_SORT = 3u << 12,    /* tile sort by bin + segmented reduce */
-    BN_STRATEGY_MASK = 15u << 12
+    BN_STRATEGY_MASK = 15u << 12,
+
+    /* Warp aggregation in the global-atomic strategy (bits 16-17): lanes of a
+     * warp that hit the same bin combine before their atomics. It pays off
+     * for clustered data and costs a warp-wide match per step otherwise. */
+    BN_AGG_AUTO = 0u << 16,
+    BN_AGG_ON = 1u << 16,
+    BN_AGG_OFF = 2u << 16,
+    BN_AGG_MASK = 3u << 16
 };
 
 /*

@@ -22,6 +22,7 @@ from ._abi import (CTX_PROFILE, ALLOC_CUDA_ASYNC, ALLOC_EXTERNAL, ALLOC_HOST, AL
                    MAX_BINS, MAX_RES, NOT_READY, OK, OP_ACCUMULATE, OP_ALL, OP_AVG, OP_COUNT,
                    OP_MAX, OP_MIN, OP_SUM, STRATEGY_AUTO, STRATEGY_GLOBAL, STRATEGY_MASK,
                    STRATEGY_PRIVATE, STRATEGY_SORT, SUM_F32, SUM_F32C, SUM_F64, SUM_MASK, U64,
+                   AGG_AUTO, AGG_ON, AGG_OFF, AGG_MASK,
                    bn_block, bn_buffer, bn_grid, bn_options, bn_result, bn_server_options,
                    bn_server_stats)
 

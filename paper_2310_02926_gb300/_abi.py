@@ -46,6 +46,10 @@ STRATEGY_PRIVATE = 1 << 12
 STRATEGY_GLOBAL = 2 << 12
 STRATEGY_SORT = 3 << 12
 STRATEGY_MASK = 15 << 12
+AGG_AUTO = 0 << 16
+AGG_ON = 1 << 16
+AGG_OFF = 2 << 16
+AGG_MASK = 3 << 16
 
 DELETER = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 

@@ -1,14 +1,508 @@
 // batch.cu -- bn_bin_batch: many independent blocks in one request (the 90
 // binning operations per in situ step of Sec. 4.3).
+//
+// Fast path (every block's columns and outputs on the context's device,
+// contiguous, explicit bounds): one persistent launch over all blocks
+// (k_batch.cu) between one init/edge launch and one finalise launch. The
+// launches are captured once per plan shape in a CUDA graph; a later batch
+// with the same shape (block sizes, meshes, strategies) only rewrites the
+// block descriptors in pinned memory and replays the graph.
+//
+// Autotuner: blocks fall into shape classes (dtype, attributes, ops, log2
+// of the bin count, log2 of the particle count). The first block of a new
+// class is binned once with each candidate strategy (shared-memory private
+// mesh if it fits; global atomics with and without warp aggregation) by the
+// batch kernel itself, timed with CUDA events, and the fastest is kept for
+// the class. CTA tiling follows from the strategy and the block size: a
+// private item carries enough particles per bin to amortise clearing and
+// merging its mesh, and large blocks are cut so every SM gets work.
+//
+// Anything else (host or strided columns, automatic bounds, mixed types)
+// takes the general path: each block queued as in bn_bin_particles.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <map>
+#include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
+#include <vector>
 
 #include "bn_runtime.h"
 
 using namespace bn;
+
+namespace {
+
+struct ClassKey {
+    int dtype, n_attrs;
+    uint32_t ops;
+    int lb, ln;
+    bool operator<(const ClassKey& o) const {
+        return std::tie(dtype, n_attrs, ops, lb, ln) < std::tie(o.dtype, o.n_attrs, o.ops, o.lb, o.ln);
+    }
+};
+
+struct Choice {
+    int strategy;
+    int aggregate;
+};
+
+// Cached graph of one plan shape, with the device and pinned memory it uses.
+struct BatchGraph {
+    std::vector<int64_t> shape;
+    cudaGraphExec_t exec = nullptr;
+    void* dev = nullptr;
+    void* host = nullptr;
+    BatchBlock* h_blocks = nullptr;
+    BatchBlock* d_blocks = nullptr;
+    cudaEvent_t last = nullptr;  // completion of the last replay (pinned buffer reuse)
+    uint64_t launches = 0;       // kernels per replay
+    ~BatchGraph() {
+        if (last) cudaEventSynchronize(last), cudaEventDestroy(last);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (dev) cudaFree(dev);
+        if (host) cudaFreeHost(host);
+    }
+};
+
+struct BatchCache {
+    std::mutex mu;
+    std::map<ClassKey, Choice> choices;
+    std::vector<std::unique_ptr<BatchGraph>> graphs;  // most recent last
+};
+
+std::mutex g_cache_mu;
+std::map<bn_context*, std::unique_ptr<BatchCache>> g_caches;
+
+BatchCache& cache_of(bn_context* c) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto& p = g_caches[c];
+    if (!p) p.reset(new BatchCache());
+    return *p;
+}
+
+int ilog2(int64_t v) {
+    int r = 0;
+    while (v > 1) v >>= 1, ++r;
+    return r;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Particles per work item for a block and strategy (the CTA tiling).
+int64_t choose_tile(int strategy, int64_t n, int64_t bins, int num_sms) {
+    if (strategy == BN_STRATEGY_PRIVATE) {
+        // at least 8 particles per bin so clearing and merging the mesh is
+        // amortised, at least 32K, and no more items than 2 per SM need
+        int64_t t = std::max<int64_t>(8 * bins, 32768);
+        t = std::max<int64_t>(t, (n + 2 * num_sms - 1) / (2 * num_sms));
+        return std::min<int64_t>(t, std::max<int64_t>(n, 1));
+    }
+    int64_t t = (n + 4 * num_sms - 1) / (4 * num_sms);
+    t = std::min<int64_t>(std::max<int64_t>(t, 16384), 262144);
+    return std::max<int64_t>(std::min<int64_t>(t, n), 1);
+}
+
+}  // namespace
+
+namespace bn {
+
+// Release the batch caches of a context (called from bn_context_destroy).
+void batch_cache_release(bn_context* c) {
+    std::unique_ptr<BatchCache> p;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        auto it = g_caches.find(c);
+        if (it == g_caches.end()) return;
+        p = std::move(it->second);
+        g_caches.erase(it);
+    }
+}
+
+}  // namespace bn
+
+// Everything the fast path needs per block, validated.
+struct FastBlock {
+    BatchBlock bb;
+    int64_t bins;
+    int64_t edges;  // f64: res_x + res_y + 2
+    ClassKey cls;
+};
+
+static bool fast_eligible(bn_context* c, const bn_block* blocks, int n_blocks) {
+    if (n_blocks < 1) return false;
+    const int dtype = blocks[0].x.dtype;
+    const int A = blocks[0].n_attrs;
+    for (int k = 0; k < n_blocks; ++k) {
+        const bn_block& b = blocks[k];
+        if (b.x.dtype != dtype || b.n_attrs != A || b.grid.auto_bounds) return false;
+        const bn_buffer* cols[2 + BN_MAX_ATTR] = {&b.x, &b.y};
+        for (int a = 0; a < b.n_attrs; ++a) cols[2 + a] = &b.attrs[a];
+        for (int j = 0; j < 2 + b.n_attrs; ++j)
+            if (cols[j]->n > 0 && (cols[j]->device != c->device || cols[j]->stride > 1)) return false;
+        const bn_result* o = b.out;
+        const bn_buffer* outs[1 + 4 * BN_MAX_ATTR] = {&o->count};
+        int no = 1;
+        for (int a = 0; a < b.n_attrs; ++a) {
+            outs[no++] = &o->sum[a];
+            outs[no++] = &o->min[a];
+            outs[no++] = &o->max[a];
+            outs[no++] = &o->avg[a];
+        }
+        for (int j = 0; j < no; ++j)
+            if (outs[j]->ptr && (outs[j]->device != c->device || outs[j]->stride > 1)) return false;
+    }
+    return true;
+}
+
+// Queue prepare + persistent bin + finalize for `fb` (used for the graph
+// capture and for autotuner trials). Device arrays must be filled.
+static cudaError_t queue_batch(const KernelCtx& kc, int dtype, int sum_mode, int n_attrs,
+                               BatchBlock* d_blocks, const int64_t* d_bin_start,
+                               const int64_t* d_edge_start, const int4* d_items, int* d_counter,
+                               int nblk, int n_items, int64_t total_bins, int64_t total_edges,
+                               size_t smem, bool want_avg) {
+    cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), kc.stream);
+    if (e == cudaSuccess)
+        e = launch_batch_prepare(kc, dtype, d_blocks, d_bin_start, d_edge_start, nblk, total_bins, total_edges);
+    if (e == cudaSuccess && n_items > 0)
+        e = launch_batch_bin(kc, dtype, sum_mode, d_blocks, d_items, n_items, d_counter, n_attrs, smem);
+    if (e == cudaSuccess && want_avg) e = launch_batch_finalize(kc, d_blocks, d_bin_start, nblk, total_bins);
+    return e;
+}
+
+// Layout of the per-plan device block: descriptors, starts, items, counter, edges.
+struct PlanLayout {
+    size_t off_blocks, off_bin_start, off_edge_start, off_items, off_counter, off_edges, bytes;
+};
+
+static PlanLayout layout_for(int nblk, int n_items, int64_t total_edges) {
+    PlanLayout L;
+    size_t o = 0;
+    L.off_blocks = o;
+    o += align256(sizeof(BatchBlock) * nblk);
+    L.off_bin_start = o;
+    o += align256(sizeof(int64_t) * (nblk + 1));
+    L.off_edge_start = o;
+    o += align256(sizeof(int64_t) * (nblk + 1));
+    L.off_items = o;
+    o += align256(sizeof(int4) * std::max(n_items, 1));
+    L.off_counter = o;
+    o += 256;
+    L.off_edges = o;
+    o += align256(sizeof(long long) * std::max<int64_t>(total_edges, 1));
+    L.bytes = o;
+    return L;
+}
+
+// Build items, starts and the per-block edge pointers for a plan in `host`
+// (pinned, layout L) whose device copy lives at `dev`.
+static void fill_plan(std::vector<FastBlock>& fbs, const PlanLayout& L, unsigned char* host,
+                      unsigned char* dev, int* n_items_out, int64_t* bins_out, int64_t* edges_out,
+                      int dtype) {
+    int64_t* bs = reinterpret_cast<int64_t*>(host + L.off_bin_start);
+    int64_t* es = reinterpret_cast<int64_t*>(host + L.off_edge_start);
+    int4* items = reinterpret_cast<int4*>(host + L.off_items);
+    long long* d_edges = reinterpret_cast<long long*>(dev + L.off_edges);
+    int64_t bins = 0, edges = 0;
+    const int nblk = (int)fbs.size();
+    for (int k = 0; k < nblk; ++k) {
+        bs[k] = bins;
+        es[k] = edges;
+        FastBlock& f = fbs[k];
+        if (dtype == BN_F64) {
+            f.bb.g.edges[0] = d_edges + edges;
+            f.bb.g.edges[1] = d_edges + edges + f.bb.g.ax[0].res + 1;
+            edges += f.edges;
+        }
+        bins += f.bins;
+    }
+    bs[nblk] = bins;
+    es[nblk] = edges;
+    // items: largest blocks first so the long ones start early
+    std::vector<int> order(nblk);
+    for (int k = 0; k < nblk; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return fbs[a].bb.n > fbs[b].bb.n; });
+    int ni = 0;
+    for (int k : order) {
+        const FastBlock& f = fbs[k];
+        if (f.bb.n == 0) continue;
+        const int64_t parts = (f.bb.n + f.bb.tile - 1) / f.bb.tile;
+        for (int64_t j = 0; j < parts; ++j) items[ni++] = make_int4(k, (int)j, 0, 0);
+    }
+    BatchBlock* hb = reinterpret_cast<BatchBlock*>(host + L.off_blocks);
+    for (int k = 0; k < nblk; ++k) hb[k] = fbs[k].bb;
+    *n_items_out = ni;
+    *bins_out = bins;
+    *edges_out = edges;
+}
+
+static int count_items(const std::vector<FastBlock>& fbs) {
+    int64_t ni = 0;
+    for (const FastBlock& f : fbs)
+        if (f.bb.n > 0) ni += (f.bb.n + f.bb.tile - 1) / f.bb.tile;
+    return (int)ni;
+}
+
+// Time one block alone with one strategy (autotuner trial), on the context
+// stream; the block's outputs are overwritten (the batch recomputes them).
+static float trial(bn_context* c, FastBlock f, int strategy, int aggregate, int dtype, int sum_mode,
+                   int n_attrs, size_t smem, bool want_avg) {
+    f.bb.strategy = strategy;
+    f.bb.aggregate = aggregate;
+    f.bb.tile = choose_tile(strategy, f.bb.n, f.bins, c->num_sms);
+    std::vector<FastBlock> one{f};
+    const int n_items = count_items(one);
+    PlanLayout L = layout_for(1, n_items, f.edges);
+    void* dev = nullptr;
+    void* host = nullptr;
+    float ms = -1.0f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMallocAsync(&dev, L.bytes, c->stream) != cudaSuccess) return -1.0f;
+    if (cudaHostAlloc(&host, L.bytes, cudaHostAllocDefault) == cudaSuccess &&
+        cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        int ni;
+        int64_t bins, edges;
+        fill_plan(one, L, static_cast<unsigned char*>(host), static_cast<unsigned char*>(dev), &ni,
+                  &bins, &edges, dtype);
+        unsigned char* d = static_cast<unsigned char*>(dev);
+        const KernelCtx kc{c->stream, c->num_sms, c->smem_optin, nullptr};
+        cudaError_t e = cudaMemcpyAsync(dev, host, L.bytes, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess)
+            e = queue_batch(kc, dtype, sum_mode, n_attrs, reinterpret_cast<BatchBlock*>(d + L.off_blocks),
+                            reinterpret_cast<int64_t*>(d + L.off_bin_start),
+                            reinterpret_cast<int64_t*>(d + L.off_edge_start),
+                            reinterpret_cast<int4*>(d + L.off_items), reinterpret_cast<int*>(d + L.off_counter),
+                            1, ni, bins, edges, smem, want_avg);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    }
+    cudaFreeAsync(dev, c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (host) cudaFreeHost(host);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return ms;
+}
+
+static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks, uint32_t ops,
+                            bn_request* r, Plan& plan) {
+    const int dtype = blocks[0].x.dtype;
+    const int A = blocks[0].n_attrs;
+    const uint32_t sum_bits = ops & BN_SUM_MASK;
+    const int sum_mode = dtype == BN_F64 ? kSumF64 : sum_bits == BN_SUM_F32 ? kSumF32
+                                                   : sum_bits == BN_SUM_F64 ? kSumF64 : kSumF32C;
+    const bool want_avg = ops & BN_OP_AVG, want_sum = ops & BN_OP_SUM;
+    const bool want_min = ops & BN_OP_MIN, want_max = ops & BN_OP_MAX, want_count = ops & BN_OP_COUNT;
+    const uint32_t forced = ops & BN_STRATEGY_MASK;
+    const uint32_t agg = ops & BN_AGG_MASK;
+    if (ops & BN_OP_ACCUMULATE) return fail(BN_ERR_INVALID_ARG, "bn_bin_batch: accumulate is not supported for batches");
+    const int dyn_limit = c->smem_optin - 1024;  // room for static shared memory
+
+    std::vector<FastBlock> fbs((size_t)n_blocks);
+    for (int k = 0; k < n_blocks; ++k) {
+        const bn_block& b = blocks[k];
+        FastBlock& f = fbs[k];
+        memset(&f.bb, 0, sizeof f.bb);
+        const int64_t n = b.x.n;
+        bn_status st = validate_buffer(c, &b.x, n, dtype, "x");
+        if (st == BN_OK) st = validate_buffer(c, &b.y, n, dtype, "y");
+        for (int a = 0; a < A && st == BN_OK; ++a) st = validate_buffer(c, &b.attrs[a], n, dtype, "attr");
+        if (st == BN_OK) st = make_grid_desc(&b.grid, dtype, &f.bb.g);
+        if (st != BN_OK) return fail(st, "bn_bin_batch: block %d: %s", k, bn_last_error());
+        for (int a = 0; a < 2; ++a) {
+            AxisDesc& d = f.bb.g.ax[a];
+            const double dl = dtype == BN_F64 ? host_fast_delta(d.lo, d.hi, d.s, d.res) : -1.0;
+            d.fast = dl >= 0.0 ? 1 : 0;
+            float fd = (float)dl;
+            if ((double)fd < dl) fd = nextafterf(fd, INFINITY);
+            d.delta = dl >= 0.0 ? fd : 0.0f;
+        }
+        for (int j = 0; j < 2; ++j) plan.wait_on(j == 0 ? b.x.stream : b.y.stream);
+        for (int a = 0; a < A; ++a) plan.wait_on(b.attrs[a].stream);
+        f.bb.x = b.x.ptr;
+        f.bb.y = b.y.ptr;
+        for (int a = 0; a < A; ++a) f.bb.a[a] = b.attrs[a].ptr;
+        f.bb.n = n;
+        f.bins = (int64_t)b.grid.res[0] * b.grid.res[1];
+        f.edges = dtype == BN_F64 ? (int64_t)b.grid.res[0] + b.grid.res[1] + 2 : 0;
+        StateDesc& sd = f.bb.st;
+        sd.bins = f.bins;
+        sd.n_attrs = A;
+        sd.do_sum = (want_sum || want_avg) ? 1 : 0;
+        sd.do_min = want_min;
+        sd.do_max = want_max;
+        sd.do_avg = want_avg;
+        void* p = nullptr;
+        st = plan.output(&b.out->count, want_count, f.bins, BN_U64, false, &p);
+        sd.count = static_cast<unsigned long long*>(p);
+        for (int a = 0; a < A && st == BN_OK; ++a) {
+            if (sd.do_sum) {
+                st = plan.output(&b.out->sum[a], want_sum, f.bins, BN_F64, false, &p);
+                sd.sum[a] = static_cast<double*>(p);
+            }
+            if (st == BN_OK && want_min) st = plan.output(&b.out->min[a], true, f.bins, dtype, false, &sd.mn[a]);
+            if (st == BN_OK && want_max) st = plan.output(&b.out->max[a], true, f.bins, dtype, false, &sd.mx[a]);
+            if (st == BN_OK && want_avg) {
+                st = plan.output(&b.out->avg[a], true, f.bins, BN_F64, false, &p);
+                sd.avg[a] = static_cast<double*>(p);
+            }
+        }
+        if (st != BN_OK) return st;
+        f.cls = ClassKey{dtype, A, ops & (BN_OP_ALL | BN_SUM_MASK), ilog2(f.bins), ilog2(std::max<int64_t>(n, 1))};
+    }
+
+    // ---- autotuner: strategy per block
+    BatchCache& cache = cache_of(c);
+    size_t smem = 0;
+    for (int k = 0; k < n_blocks; ++k) {
+        FastBlock& f = fbs[k];
+        const size_t mesh = private_mesh_bytes(dtype, sum_mode, f.bins, A, f.bb.st.do_sum, want_min, want_max);
+        const bool fits = mesh <= (size_t)dyn_limit && f.bins <= (1 << 20);
+        Choice ch{BN_STRATEGY_GLOBAL, f.bins <= 65536 ? 1 : 0};
+        if (forced == BN_STRATEGY_PRIVATE) {
+            if (!fits) return fail(BN_ERR_INVALID_ARG, "bn_bin_batch: block %d mesh does not fit shared memory", k);
+            ch.strategy = BN_STRATEGY_PRIVATE;
+        } else if (forced == BN_STRATEGY_GLOBAL || forced == BN_STRATEGY_SORT) {
+            ch.strategy = BN_STRATEGY_GLOBAL;
+        } else {
+            std::lock_guard<std::mutex> lk(cache.mu);
+            auto it = cache.choices.find(f.cls);
+            if (it != cache.choices.end()) {
+                ch = it->second;
+                if (ch.strategy == BN_STRATEGY_PRIVATE && !fits) ch.strategy = BN_STRATEGY_GLOBAL;
+            } else if (f.bb.n > 0) {
+                float best = -1.0f;
+                const int cands[3][2] = {{BN_STRATEGY_PRIVATE, 0}, {BN_STRATEGY_GLOBAL, 0}, {BN_STRATEGY_GLOBAL, 1}};
+                for (auto& cd : cands) {
+                    if (cd[0] == BN_STRATEGY_PRIVATE && !fits) continue;
+                    const float ms = trial(c, f, cd[0], cd[1], dtype, sum_mode, A,
+                                           cd[0] == BN_STRATEGY_PRIVATE ? mesh : 0, want_avg);
+                    if (ms >= 0.0f && (best < 0.0f || ms < best)) {
+                        best = ms;
+                        ch = Choice{cd[0], cd[1]};
+                    }
+                }
+                cache.choices[f.cls] = ch;
+            }
+        }
+        if (agg == BN_AGG_ON) ch.aggregate = 1;
+        if (agg == BN_AGG_OFF) ch.aggregate = 0;
+        f.bb.strategy = ch.strategy;
+        f.bb.aggregate = ch.aggregate;
+        f.bb.tile = choose_tile(ch.strategy, f.bb.n, f.bins, c->num_sms);
+        if (ch.strategy == BN_STRATEGY_PRIVATE) smem = std::max(smem, mesh);
+    }
+
+    // ---- plan shape and graph
+    std::vector<int64_t> shape;
+    shape.reserve(4 + 5 * (size_t)n_blocks);
+    shape.push_back(dtype);
+    shape.push_back(A);
+    shape.push_back(ops & ~(uint32_t)BN_STRATEGY_MASK);
+    shape.push_back(n_blocks);
+    for (const FastBlock& f : fbs) {
+        shape.push_back(f.bb.n);
+        shape.push_back(f.bb.g.ax[0].res);
+        shape.push_back(f.bb.g.ax[1].res);
+        shape.push_back(f.bb.strategy * 2 + f.bb.aggregate);
+        shape.push_back(f.bb.tile);
+    }
+    const int n_items = count_items(fbs);
+    int64_t total_edges = 0;
+    for (const FastBlock& f : fbs) total_edges += f.edges;
+    PlanLayout L = layout_for(n_blocks, n_items, total_edges);
+
+    BatchGraph* G = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(cache.mu);
+        for (auto& g : cache.graphs)
+            if (g->shape == shape) G = g.get();
+    }
+    const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy;
+    if (!G) {
+        std::unique_ptr<BatchGraph> ng(new BatchGraph());
+        ng->shape = shape;
+        cudaError_t e = cudaMalloc(&ng->dev, L.bytes);
+        if (e == cudaSuccess) e = cudaHostAlloc(&ng->host, L.bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ng->last, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: plan memory");
+        int ni;
+        int64_t bins, edges;
+        fill_plan(fbs, L, static_cast<unsigned char*>(ng->host), static_cast<unsigned char*>(ng->dev), &ni,
+                  &bins, &edges, dtype);
+        ng->h_blocks = reinterpret_cast<BatchBlock*>(static_cast<unsigned char*>(ng->host) + L.off_blocks);
+        ng->d_blocks = reinterpret_cast<BatchBlock*>(static_cast<unsigned char*>(ng->dev) + L.off_blocks);
+        // the static part (starts, items) goes over once
+        e = cudaMemcpy(ng->dev, ng->host, L.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: plan upload");
+        unsigned char* d = static_cast<unsigned char*>(ng->dev);
+        std::atomic<uint64_t> nlaunch{0};
+        const KernelCtx kc{c->stream, c->num_sms, c->smem_optin, &nlaunch};
+        auto body = [&]() {
+            cudaError_t e2 = cudaMemcpyAsync(ng->d_blocks, ng->h_blocks, sizeof(BatchBlock) * n_blocks,
+                                             cudaMemcpyHostToDevice, c->stream);
+            if (e2 == cudaSuccess)
+                e2 = queue_batch(kc, dtype, sum_mode, A, ng->d_blocks, reinterpret_cast<int64_t*>(d + L.off_bin_start),
+                                 reinterpret_cast<int64_t*>(d + L.off_edge_start),
+                                 reinterpret_cast<int4*>(d + L.off_items), reinterpret_cast<int*>(d + L.off_counter),
+                                 n_blocks, ni, bins, edges, smem, want_avg);
+            return e2;
+        };
+        if (capturable) {
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            cudaError_t eb = e == cudaSuccess ? body() : e;
+            cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+            if (e == cudaSuccess) e = eb != cudaSuccess ? eb : ee;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ng->exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: graph capture");
+            ng->launches = nlaunch.load();
+        }
+        std::lock_guard<std::mutex> lk(cache.mu);
+        cache.graphs.push_back(std::move(ng));
+        if (cache.graphs.size() > 8) cache.graphs.erase(cache.graphs.begin());
+        G = cache.graphs.back().get();
+        if (!capturable) {
+            // no graph on the legacy stream: launch directly
+            cudaError_t e2 = body();
+            if (e2 != cudaSuccess) return cuda_fail(e2, "bn_bin_batch: launch");
+            c->launches.fetch_add(nlaunch.load());
+            cudaEventRecord(G->last, c->stream);
+            return BN_OK;
+        }
+    } else {
+        // same shape: wait until the pinned descriptors are free, rewrite them
+        cudaEventSynchronize(G->last);
+        unsigned char* host = static_cast<unsigned char*>(G->host);
+        int4* unused_items = nullptr;
+        (void)unused_items;
+        int64_t edge_off = 0;
+        for (int k = 0; k < n_blocks; ++k) {
+            FastBlock& f = fbs[k];
+            if (dtype == BN_F64) {
+                long long* d_edges = reinterpret_cast<long long*>(static_cast<unsigned char*>(G->dev) + L.off_edges);
+                f.bb.g.edges[0] = d_edges + edge_off;
+                f.bb.g.edges[1] = d_edges + edge_off + f.bb.g.ax[0].res + 1;
+                edge_off += f.edges;
+            }
+            reinterpret_cast<BatchBlock*>(host + L.off_blocks)[k] = f.bb;
+        }
+    }
+    cudaError_t e = cudaGraphLaunch(G->exec, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: graph launch");
+    c->launches.fetch_add(G->launches);
+    cudaEventRecord(G->last, c->stream);
+    (void)r;
+    return BN_OK;
+}
 
 extern "C" bn_status bn_bin_batch(bn_context* c, const bn_block* blocks, int n_blocks,
                                   uint32_t ops, int sync, bn_request** req) {
@@ -16,8 +510,11 @@ extern "C" bn_status bn_bin_batch(bn_context* c, const bn_block* blocks, int n_b
     if (!sync && !req) return fail(BN_ERR_INVALID_ARG, "bn_bin_batch: asynchronous call needs req");
     if (n_blocks < 0 || (n_blocks > 0 && !blocks)) return fail(BN_ERR_INVALID_ARG, "bn_bin_batch: bad blocks");
     if (req) *req = nullptr;
-    for (int k = 0; k < n_blocks; ++k)
+    for (int k = 0; k < n_blocks; ++k) {
         if (!blocks[k].out) return fail(BN_ERR_INVALID_ARG, "bn_bin_batch: block %d has no outputs", k);
+        if (blocks[k].n_attrs < 0 || blocks[k].n_attrs > BN_MAX_ATTR)
+            return fail(BN_ERR_INVALID_ARG, "bn_bin_batch: block %d: bad n_attrs", k);
+    }
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != c->device) cudaSetDevice(c->device);
@@ -26,10 +523,14 @@ extern "C" bn_status bn_bin_batch(bn_context* c, const bn_block* blocks, int n_b
     if (!r) return fail(BN_ERR_NO_MEMORY, "bn_bin_batch: no request slot");
     Plan plan(c);
     bn_status st = BN_OK;
-    for (int k = 0; k < n_blocks && st == BN_OK; ++k) {
-        const bn_block& b = blocks[k];
-        st = enqueue_bin(c, plan, &b.x, &b.y, b.attrs, b.n_attrs, &b.grid, ops, b.out,
-                         c->status_dev + r->slot);
+    if (fast_eligible(c, blocks, n_blocks)) {
+        st = batch_fast(c, blocks, n_blocks, ops, r, plan);
+    } else {
+        for (int k = 0; k < n_blocks && st == BN_OK; ++k) {
+            const bn_block& b = blocks[k];
+            st = enqueue_bin(c, plan, &b.x, &b.y, b.attrs, b.n_attrs, &b.grid, ops, b.out,
+                             c->status_dev + r->slot);
+        }
     }
     if (st == BN_OK) st = plan.finish(r);
     if (st != BN_OK) {

@@ -1,0 +1,325 @@
+// bn_device.cuh -- device-side building blocks shared by the particle-pass
+// kernels: vector column loads, the exact mesh locator, and the shared-
+// memory mesh (count, sums, min, max of a range of bins).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "bn_internal.cuh"
+
+namespace bn {
+
+template <typename T> struct VecOf;
+template <> struct VecOf<float> { using type = float4; static constexpr int N = 4; };
+template <> struct VecOf<double> { using type = double2; static constexpr int N = 2; };
+
+template <typename T>
+__device__ __forceinline__ T vget(const typename VecOf<T>::type& v, int j);
+template <> __device__ __forceinline__ float vget<float>(const float4& v, int j) {
+    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+template <> __device__ __forceinline__ double vget<double>(const double2& v, int j) {
+    return j == 0 ? v.x : v.y;
+}
+
+// Mesh location of a particle, -1 when outside.
+template <typename T> struct Binner;
+template <> struct Binner<float> {
+    Axis<float> ax, ay;
+    int rx;
+    __device__ void init(const GridDesc& g) {
+        ax = make_axis<float>(g.ax[0]);
+        ay = make_axis<float>(g.ax[1]);
+        rx = g.ax[0].res;
+    }
+    __device__ __forceinline__ int bin(float x, float y) const {
+        int ix = axis_bin(ax, x);
+        int iy = axis_bin(ay, y);
+        return (ix < 0 || iy < 0) ? -1 : iy * rx + ix;
+    }
+};
+template <> struct Binner<double> {
+    AxisF64 ax, ay;
+    int rx;
+    __device__ void init(const GridDesc& g) {
+        ax = make_axis_f64(g.ax[0], g.edges[0]);
+        ay = make_axis_f64(g.ax[1], g.edges[1]);
+        rx = g.ax[0].res;
+    }
+    __device__ __forceinline__ int bin(double x, double y) const {
+        int ix = axis_bin(ax, x);
+        int iy = axis_bin(ay, y);
+        return (ix < 0 || iy < 0) ? -1 : iy * rx + ix;
+    }
+};
+
+// IEEE totalOrder key of a value's bits as a signed integer (-0 < +0):
+// non-negative patterns keep their bits, negative ones flip the magnitude.
+// key_bits inverts it.
+template <typename T> struct KeyOf;
+template <> struct KeyOf<float> {
+    using K = int;
+    using K2 = int2;
+    static __device__ __forceinline__ int key(float v) {
+        const int b = __float_as_int(v);
+        return b >= 0 ? b : (b ^ 0x7fffffff);
+    }
+    static __device__ __forceinline__ float value(int k) {
+        return __int_as_float(k >= 0 ? k : (k ^ 0x7fffffff));
+    }
+    static constexpr int kPosInf = 0x7f800000;
+    static constexpr int kNegInf = (int)(0xff800000u ^ 0x7fffffffu);
+};
+template <> struct KeyOf<double> {
+    using K = long long;
+    using K2 = longlong2;
+    static __device__ __forceinline__ long long key(double v) {
+        const long long b = __double_as_longlong(v);
+        return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+    }
+    static __device__ __forceinline__ double value(long long k) {
+        return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffll));
+    }
+    static constexpr long long kPosInf = 0x7ff0000000000000ll;
+    static constexpr long long kNegInf = (long long)(0xfff0000000000000ull ^ 0x7fffffffffffffffull);
+};
+
+// Shared-memory mesh of B bins. Sums are FP64 for f64 data and for f32 data
+// in kSumF64 mode; FP32 (plus an FP32 compensation term in kSumF32C)
+// otherwise. Min and max of one attribute and bin sit next to each other
+// as totalOrder keys, so one load reads both and the updates are plain
+// signed integer atomicMin / atomicMax.
+template <typename T, int MODE>
+struct SmemMesh {
+    static constexpr bool kWide = sizeof(T) == 8 || MODE == kSumF64;
+    using KO = KeyOf<T>;
+    using K = typename KO::K;
+    using K2 = typename KO::K2;
+    unsigned int* cnt;
+    double* s64;
+    float* s32;
+    float* c32;
+    K2* mm;  // [A][B] {min key, max key}
+    int B;
+    bool do_sum, do_mm, do_min, do_max;
+
+    __device__ void carve(unsigned char* base, int B_, int A, bool s, bool lo, bool hi) {
+        B = B_;
+        do_sum = s;
+        do_min = lo;
+        do_max = hi;
+        do_mm = lo || hi;
+        size_t off = ((size_t)B * 4 + 15) & ~(size_t)15;
+        cnt = reinterpret_cast<unsigned int*>(base);
+        s64 = nullptr;
+        s32 = nullptr;
+        c32 = nullptr;
+        if (do_sum) {
+            if (kWide) {
+                s64 = reinterpret_cast<double*>(base + off);
+                off += (size_t)A * B * 8;
+            } else {
+                s32 = reinterpret_cast<float*>(base + off);
+                off += (size_t)A * B * 4;
+                if (MODE == kSumF32C) {
+                    c32 = reinterpret_cast<float*>(base + off);
+                    off += (size_t)A * B * 4;
+                }
+            }
+        }
+        off = (off + 15) & ~(size_t)15;
+        mm = do_mm ? reinterpret_cast<K2*>(base + off) : nullptr;
+    }
+
+    __device__ void clear(int A) {
+        for (int b = threadIdx.x; b < B; b += blockDim.x) cnt[b] = 0u;
+        const int AB = A * B;
+        if (do_sum) {
+            if (kWide) {
+                for (int k = threadIdx.x; k < AB; k += blockDim.x) s64[k] = 0.0;
+            } else {
+                for (int k = threadIdx.x; k < AB; k += blockDim.x) s32[k] = 0.0f;
+                if (MODE == kSumF32C)
+                    for (int k = threadIdx.x; k < AB; k += blockDim.x) c32[k] = 0.0f;
+            }
+        }
+        if (do_mm) {
+            K2 init;
+            init.x = KO::kPosInf;
+            init.y = KO::kNegInf;
+            for (int k = threadIdx.x; k < AB; k += blockDim.x) mm[k] = init;
+        }
+    }
+
+    __device__ __forceinline__ void add_count(int b) { atomicAdd(&cnt[b], 1u); }
+
+    __device__ __forceinline__ void add(int a, int b, T v) {
+        const int k = a * B + b;
+        if (do_sum) {
+            if (kWide) {
+                atomicAdd(&s64[k], (double)v);
+            } else if (MODE == kSumF32) {
+                atomicAdd(&s32[k], (float)v);
+            } else {
+                // Two-sum of the value the atomic added to: the exact rounding
+                // error of old + v goes into the compensation term.
+                float fv = (float)v;
+                float old = atomicAdd(&s32[k], fv);
+                float s = __fadd_rn(old, fv);
+                float bp = __fsub_rn(s, old);
+                float err = __fadd_rn(__fsub_rn(old, __fsub_rn(s, bp)), __fsub_rn(fv, bp));
+                // once the sum is +/-inf or NaN the error term is meaningless
+                // (inf - inf); the sum itself already carries the result
+                if (err != 0.0f && (__float_as_uint(err) & 0x7f800000u) != 0x7f800000u)
+                    atomicAdd(&c32[k], err);
+            }
+        }
+        if (do_mm) {
+            if (is_nan_bits(v)) return;
+            const K key = KO::key(v);
+            const K2 cur = mm[k];
+            if (do_min && key < cur.x) atomicMin(&mm[k].x, key);
+            if (do_max && key > cur.y) atomicMax(&mm[k].y, key);
+        }
+    }
+
+    // Sum of one bin as FP64: the FP64 accumulator, the FP32 partial, or the
+    // FP32 partial plus its compensation term (unless the partial is inf/NaN).
+    __device__ __forceinline__ double sum_value(int k) const {
+        if (kWide) return s64[k];
+        if (MODE == kSumF32) return (double)s32[k];
+        const float hi = s32[k];
+        return ((__float_as_uint(hi) & 0x7f800000u) == 0x7f800000u)
+                   ? (double)hi
+                   : __dadd_rn((double)hi, (double)c32[k]);
+    }
+
+    // CTA partial -> global mesh. Local bin l is global bin base + l; only
+    // l < nbins exist. sole: this CTA holds the complete result of these
+    // bins, so plain stores replace the atomics (empty bins included);
+    // otherwise only non-empty bins are merged.
+    __device__ void merge(const StateDesc& st, int A, int64_t base = 0, int nbins = -1,
+                          bool sole = false) {
+        const int nb = nbins < 0 ? B : nbins;
+        for (int l = threadIdx.x; l < nb; l += blockDim.x) {
+            const unsigned int c = cnt[l];
+            const int64_t b = base + l;
+            if (sole) {
+                st.count[b] = (unsigned long long)c;
+                for (int a = 0; a < A; ++a) {
+                    const int k = a * B + l;
+                    if (do_sum) st.sum[a][b] = sum_value(k);
+                    if (do_mm) {
+                        const K2 cur = mm[k];
+                        if (do_min) static_cast<T*>(st.mn[a])[b] = KO::value(cur.x);
+                        if (do_max) static_cast<T*>(st.mx[a])[b] = KO::value(cur.y);
+                    }
+                }
+                continue;
+            }
+            if (c == 0u) continue;
+            atomicAdd(&st.count[b], (unsigned long long)c);
+            for (int a = 0; a < A; ++a) {
+                const int k = a * B + l;
+                if (do_sum) atomicAdd(&st.sum[a][b], sum_value(k));
+                if (do_mm) {
+                    const K2 cur = mm[k];
+                    if (do_min) {
+                        const T m = KO::value(cur.x);
+                        T* g = static_cast<T*>(st.mn[a]) + b;
+                        if (total_less(m, __ldcg(g))) atomic_min_total(g, m);
+                    }
+                    if (do_max) {
+                        const T m = KO::value(cur.y);
+                        T* g = static_cast<T*>(st.mx[a]) + b;
+                        if (total_less(__ldcg(g), m)) atomic_max_total(g, m);
+                    }
+                }
+            }
+        }
+    }
+};
+
+// Current min/max of a bin for the read-before-atomic filter, through L1.
+// L1 is not coherent with the atomics in L2, so the value may be stale; a
+// stale min is never below the true min (mins only fall), and a stale max
+// never above the true max, so a stale read only admits extra atomics.
+template <typename T>
+__device__ __forceinline__ T filter_load(const T* p) { return __ldca(p); }
+
+// Combine the lanes of the calling warp that share bin b (b >= 0) and let
+// the lowest such lane update the global mesh. Every lane of the warp must
+// call it (b = -1 for lanes without an in-bounds particle).
+template <typename T, int A_CT>
+__device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, const T* v,
+                                            bool aggregate) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = aggregate ? __match_any_sync(full, b) : (1u << lane);
+    const int leader = __ffs(peers) - 1;
+    const bool alone = peers == (1u << lane);
+    if (!aggregate || __all_sync(full, alone || b < 0)) {
+        // no two lanes share a bin: skip the combining shuffles
+        if (b < 0) return;
+        atomicAdd(&st.count[b], 1ull);
+        for (int a = 0; a < A; ++a) {
+            const T x = v[a];
+            if (st.do_sum) atomicAdd(&st.sum[a][b], (double)x);
+            if (is_nan_bits(x)) continue;
+            if (st.do_min) {
+                T* g = static_cast<T*>(st.mn[a]) + b;
+                if (total_less(x, filter_load(g))) atomic_min_total(g, x);
+            }
+            if (st.do_max) {
+                T* g = static_cast<T*>(st.mx[a]) + b;
+                if (total_less(filter_load(g), x)) atomic_max_total(g, x);
+            }
+        }
+        return;
+    }
+    // General case: the leader of each peer group gathers its peers' values
+    // lane by lane (the loop runs over the largest group in the warp).
+    const unsigned cnt = __popc(peers);
+    double s[A_CT > 0 ? A_CT : kMaxAttr];
+    T lo[A_CT > 0 ? A_CT : kMaxAttr], hi[A_CT > 0 ? A_CT : kMaxAttr];
+    for (int a = 0; a < A; ++a) {
+        s[a] = 0.0;
+        lo[a] = pos_inf<T>();
+        hi[a] = neg_inf<T>();
+    }
+    unsigned rest = peers;
+    // every lane walks its own group; shuffles need all lanes, so loop to the
+    // warp-wide maximum group size
+    int my_n = (b >= 0) ? (int)cnt : 0;
+    int max_n = my_n;
+    for (int off = 16; off > 0; off >>= 1) max_n = max(max_n, __shfl_xor_sync(full, max_n, off));
+    for (int it = 0; it < max_n; ++it) {
+        int src = rest ? __ffs(rest) - 1 : lane;
+        if (rest) rest &= rest - 1;
+        for (int a = 0; a < A; ++a) {
+            T x = __shfl_sync(full, v[a], src);
+            if (b >= 0 && it < my_n) {
+                s[a] += (double)x;  // FP64 add in this lane's registers
+                if (!is_nan_bits(x)) {
+                    if (total_less(x, lo[a])) lo[a] = x;
+                    if (total_less(hi[a], x)) hi[a] = x;
+                }
+            }
+        }
+    }
+    if (b < 0 || lane != leader) return;
+    atomicAdd(&st.count[b], (unsigned long long)cnt);
+    for (int a = 0; a < A; ++a) {
+        if (st.do_sum) atomicAdd(&st.sum[a][b], s[a]);
+        if (st.do_min && !(lo[a] == pos_inf<T>())) {
+            T* g = static_cast<T*>(st.mn[a]) + b;
+            if (total_less(lo[a], filter_load(g))) atomic_min_total(g, lo[a]);
+        }
+        if (st.do_max && !(hi[a] == neg_inf<T>())) {
+            T* g = static_cast<T*>(st.mx[a]) + b;
+            if (total_less(filter_load(g), hi[a])) atomic_max_total(g, hi[a]);
+        }
+    }
+}
+
+}  // namespace bn

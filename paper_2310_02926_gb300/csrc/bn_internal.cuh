@@ -22,11 +22,12 @@ struct AxisDesc {
     double lo, hi, s;
     int32_t res;
     int32_t closed;
-    // f64 coordinates only: 1 when the FP32 estimate of t is within one bin
-    // of the exact t everywhere on the axis (then the edge-key correction
-    // below is exact); 0 = evaluate the reference sequence on the FP64 pipe.
+    // f64 coordinates only: 1 when the FP32 estimate of t is within `delta`
+    // bins of the exact t everywhere on the axis, with delta < 1/4 (then the
+    // estimate plus the edge-key correction below is exact); 0 = evaluate the
+    // reference sequence on the FP64 pipe.
     int32_t fast;
-    int32_t pad;
+    float delta;
 };
 
 // The mesh as the kernels see it. For explicit bounds the host fills it;
@@ -218,6 +219,8 @@ struct AxisF64 {
     const long long* E;
     long long klo, khi;  // E[0], E[res]
     float flo, fs;       // FP32 estimate parameters
+    float delta;         // bound on |estimate - t|, in bins
+    float tmax;          // res - delta
     int res;
     bool fast;
     double lo, hi, s;
@@ -235,17 +238,30 @@ __device__ __forceinline__ AxisF64 make_axis_f64(const AxisDesc& d, const long l
     a.closed = d.closed != 0;
     a.flo = approx_float(d.lo);
     a.fs = (float)d.s;
+    a.delta = d.delta;
+    a.tmax = (float)d.res - d.delta;
     a.klo = a.fast ? __ldg(E) : 0;
     a.khi = a.fast ? __ldg(E + d.res) : 0;
     return a;
 }
 
+// Exact bin of x on an f64 axis (-1 outside). Fast path: the FP32 estimate
+// t_f is within delta of the reference t, so when t_f lies in
+// (delta, res - delta) and at least delta away from the nearest integer,
+// x is inside and trunc(t) == trunc(t_f). Otherwise (about 2 * delta of the
+// particles, and every particle outside or near the ends) the ordered key
+// of x is compared with the exact edge keys.
 __device__ __forceinline__ int axis_bin(const AxisF64& a, double x) {
     if (!a.fast) return axis_bin_direct(a.lo, a.hi, a.s, a.res, a.closed, x);
-    long long k = ordered_key(x);
+    const float t = __fmul_rn(__fsub_rn(approx_float(x), a.flo), a.fs);
+    if (t > a.delta && t < a.tmax) {
+        const float fl = truncf(t);
+        const float fr = t - fl;  // exact: t and fl share the binade
+        if (fr > a.delta && fr < 1.0f - a.delta) return (int)fl;
+    }
+    const long long k = ordered_key(x);
     if (k < a.klo || k >= a.khi) return -1;  // NaN keys fall outside too
-    float t = __fmul_rn(__fsub_rn(approx_float(x), a.flo), a.fs);
-    int i = __float2int_rz(t);
+    int i = (t > 0.0f) ? __float2int_rz(t) : 0;
     i = max(0, min(i, a.res - 1));
     if (k < __ldg(a.E + i)) {
         i -= 1;
@@ -264,6 +280,60 @@ __device__ __forceinline__ int axis_bin(const AxisF64& a, double x) {
     }
     return i;
 }
+
+// ---------------------------------------------------------------- edge keys
+// Reference bin index on the FP64 pipe (used only to locate edges).
+__device__ __forceinline__ int ref_idx_f64(const AxisDesc& d, double x) {
+    double t = __dmul_rn(__dsub_rn(x, d.lo), d.s);
+    int k = __double2int_rz(t);
+    return min(k, d.res - 1);
+}
+
+__device__ __forceinline__ long long key_of(double v) { return ordered_key(v); }
+
+// E[i]: the smallest ordered key whose value has bin index >= i. The index
+// is non-decreasing in the key, so a bracketing search finds it; it starts
+// at the key of lo + i / s and gallops outwards.
+__device__ inline long long edge_key(const AxisDesc& d, int i) {
+    const long long K0 = key_of(d.lo);
+    const long long Khi = key_of(d.hi) + (d.closed ? 1 : 0);
+    if (i <= 0) return K0;
+    if (i >= d.res) return Khi;
+    // invariant: f(lo_k) false (index < i), f(hi_k) true (index >= i; Khi by
+    // convention since hi itself indexes to res - 1 >= i)
+    long long lo_k = K0, hi_k = Khi;
+    auto f = [&](long long k) { return ref_idx_f64(d, key_to_double(k)) >= i; };
+    auto gap = [&]() { return (unsigned long long)hi_k - (unsigned long long)lo_k; };
+    if (gap() > 2) {
+        double est = __dadd_rn(d.lo, __ddiv_rn((double)i, d.s));
+        long long e = key_of(est);
+        if (e <= lo_k) e = lo_k + 1;
+        if (e >= hi_k) e = hi_k - 1;
+        if (f(e)) {
+            hi_k = e;
+            unsigned long long step = 1;
+            for (int it = 0; it < 64 && gap() > 1; ++it) {
+                if (step >= gap()) break;
+                long long c = hi_k - (long long)step;
+                if (f(c)) { hi_k = c; step <<= 1; } else { lo_k = c; break; }
+            }
+        } else {
+            lo_k = e;
+            unsigned long long step = 1;
+            for (int it = 0; it < 64 && gap() > 1; ++it) {
+                if (step >= gap()) break;
+                long long c = lo_k + (long long)step;
+                if (f(c)) { hi_k = c; break; } else { lo_k = c; step <<= 1; }
+            }
+        }
+    }
+    for (int it = 0; it < 70 && gap() > 1; ++it) {
+        long long mid = lo_k + (long long)(gap() >> 1);
+        if (f(mid)) hi_k = mid; else lo_k = mid;
+    }
+    return hi_k;
+}
+
 
 // ---------------------------------------------------------------- launch info
 struct LaunchCfg {

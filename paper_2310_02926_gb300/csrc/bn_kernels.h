@@ -34,13 +34,14 @@ cudaError_t launch_merge(const KernelCtx& kc, int dtype, const StateDesc& out,
                          const StateDesc* dev_parts, int n_parts);
 cudaError_t launch_gather(const KernelCtx& kc, int dtype, void* dst, const void* src, int64_t n,
                           int64_t stride);
-int host_fast_ok(double lo, double hi, double s, int res);
+double host_fast_delta(double lo, double hi, double s, int res);
 
 // Hot loop: one pass over the particles into the per-bin state.
 struct BinArgs {
     int dtype;              // BN_F32 / BN_F64
     int n_attrs;
     int sum_mode;           // SumMode (f32 data)
+    int aggregate;          // global strategy: combine same-bin lanes of a warp first
     const void* x;
     const void* y;
     const void* a[kMaxAttr];
@@ -49,6 +50,54 @@ struct BinArgs {
     const GridDesc* dev_grid;  // ... or read on the device (automatic bounds; null otherwise)
     StateDesc st;
 };
+
+// Plan of the bucketed sort + reduce (k_sort.cu). Sizes are set by
+// sort_plan; the device pointers by launch_bin_sort from one scratch block.
+struct SortDesc {
+    int log2bk;        // bins per bucket = 1 << log2bk
+    int nb;            // buckets
+    int tp;            // particles per pass-1 tile
+    int chunk;         // records per pass-2 work item (about)
+    int64_t tiles;     // pass-1 tiles
+    int64_t slots;     // tiles * tp record slots
+    int64_t max_items;
+    int off_skey, off_sattr, off_mesh, pad;
+    size_t smem_scatter, smem_reduce;
+    unsigned short* keys;  // [slots] bin within bucket
+    void* attrs;           // [n_attrs][slots] attribute values
+    int* table;            // [tiles][nb + 1] bucket offsets within each tile
+    int* table_t;          // [nb + 1][tiles] the same, transposed
+    int* bucket_total;     // [nb]
+    int4* items;           // [max_items] {bucket, tile0, tile1, sole}
+    int* counters;         // [0] items, [1] next item to take
+};
+
+bool sort_plan(const BinArgs& a, int smem_optin, SortDesc* sd);
+size_t sort_scratch_bytes(const SortDesc& sd, const BinArgs& a);
+cudaError_t launch_bin_sort(const KernelCtx& kc, const BinArgs& a, SortDesc sd, void* scratch);
+
+// One block of a batch as the persistent kernel sees it (k_batch.cu).
+struct BatchBlock {
+    const void* x;
+    const void* y;
+    const void* a[kMaxAttr];
+    int64_t n;
+    int64_t tile;      // particles per work item
+    GridDesc g;        // explicit bounds; edges point into the batch scratch (f64)
+    StateDesc st;      // the block's outputs
+    int strategy;      // BN_STRATEGY_PRIVATE or BN_STRATEGY_GLOBAL
+    int aggregate;
+    int pad[2];
+};
+
+cudaError_t launch_batch_prepare(const KernelCtx& kc, int dtype, BatchBlock* dev_blocks,
+                                 const int64_t* dev_bin_start, const int64_t* dev_edge_start,
+                                 int nblk, int64_t total_bins, int64_t total_edges);
+cudaError_t launch_batch_bin(const KernelCtx& kc, int dtype, int sum_mode, const BatchBlock* blocks,
+                             const int4* items, int n_items, int* counter, int n_attrs, size_t smem);
+cudaError_t launch_batch_finalize(const KernelCtx& kc, const BatchBlock* dev_blocks,
+                                  const int64_t* dev_bin_start, int nblk, int64_t total_bins);
+size_t private_mesh_bytes(int dtype, int sum_mode, int64_t bins, int n_attrs, bool s, bool lo, bool hi);
 
 // Shared-memory bytes the privatised kernel needs for this mesh, or 0 if
 // the mesh does not fit.

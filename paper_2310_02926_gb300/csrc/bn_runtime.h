@@ -105,5 +105,6 @@ bn_status enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const bn_bu
                       const bn_buffer* attrs, int n_attrs, const bn_grid* grid, uint32_t ops,
                       bn_result* out, int* status_dev);
 bn_status complete_sync(bn_request* r, int sync, bn_request** req);
+void batch_cache_release(bn_context* c);
 
 }  // namespace bn

@@ -100,58 +100,6 @@ __global__ void k_bounds_reduce(const T* __restrict__ x, const T* __restrict__ y
 }
 
 // ------------------------------------------------------------------ set-up
-// Reference bin index on the FP64 pipe (used only to locate edges).
-__device__ __forceinline__ int ref_idx_f64(const AxisDesc& d, double x) {
-    double t = __dmul_rn(__dsub_rn(x, d.lo), d.s);
-    int k = __double2int_rz(t);
-    return min(k, d.res - 1);
-}
-
-__device__ __forceinline__ long long key_of(double v) { return ordered_key(v); }
-
-// E[i]: the smallest ordered key whose value has bin index >= i. The index
-// is non-decreasing in the key, so a bracketing search finds it; it starts
-// at the key of lo + i / s and gallops outwards.
-__device__ long long edge_key(const AxisDesc& d, int i) {
-    const long long K0 = key_of(d.lo);
-    const long long Khi = key_of(d.hi) + (d.closed ? 1 : 0);
-    if (i <= 0) return K0;
-    if (i >= d.res) return Khi;
-    // invariant: f(lo_k) false (index < i), f(hi_k) true (index >= i; Khi by
-    // convention since hi itself indexes to res - 1 >= i)
-    long long lo_k = K0, hi_k = Khi;
-    auto f = [&](long long k) { return ref_idx_f64(d, key_to_double(k)) >= i; };
-    auto gap = [&]() { return (unsigned long long)hi_k - (unsigned long long)lo_k; };
-    if (gap() > 2) {
-        double est = __dadd_rn(d.lo, __ddiv_rn((double)i, d.s));
-        long long e = key_of(est);
-        if (e <= lo_k) e = lo_k + 1;
-        if (e >= hi_k) e = hi_k - 1;
-        if (f(e)) {
-            hi_k = e;
-            unsigned long long step = 1;
-            for (int it = 0; it < 64 && gap() > 1; ++it) {
-                if (step >= gap()) break;
-                long long c = hi_k - (long long)step;
-                if (f(c)) { hi_k = c; step <<= 1; } else { lo_k = c; break; }
-            }
-        } else {
-            lo_k = e;
-            unsigned long long step = 1;
-            for (int it = 0; it < 64 && gap() > 1; ++it) {
-                if (step >= gap()) break;
-                long long c = lo_k + (long long)step;
-                if (f(c)) { hi_k = c; break; } else { lo_k = c; step <<= 1; }
-            }
-        }
-    }
-    for (int it = 0; it < 70 && gap() > 1; ++it) {
-        long long mid = lo_k + (long long)(gap() >> 1);
-        if (f(mid)) hi_k = mid; else lo_k = mid;
-    }
-    return hi_k;
-}
-
 template <typename T>
 __device__ bool make_axis_from_bounds(T lo, T hi, int res, AxisDesc* d) {
     // Sec. 4.2 automatic bounds: [min, max] of the finite coordinates, closed.
@@ -174,13 +122,17 @@ __device__ bool make_axis_from_bounds(T lo, T hi, int res, AxisDesc* d) {
     return true;
 }
 
-// The FP32 estimate of t is off by at most about (|x| + |lo|) * s * 2^-19
-// plus a few FP32 roundings of t; when that stays below half a bin the
-// one-step edge correction is exact.
-__device__ __host__ inline int fast_ok(double lo, double hi, double s, int res) {
+// Bound on |t_f - t| in bins for the FP32 estimate of an f64 axis: x and lo
+// are truncated to 20 mantissa bits (each off by at most 2^-20 of its
+// magnitude m, times s), and the FP32 subtraction, the rounding of s to FP32
+// and the FP32 multiplication each add at most 2^-24 * res; the reference t
+// itself is within a few 2^-53 * res of the real value. The bound below
+// doubles each term. Returns the bound, or a negative value when the
+// estimate is not usable (bound >= 1/4, or values outside FP32 range).
+__device__ __host__ inline double fast_delta(double lo, double hi, double s, int res) {
     double m = fabs(lo) > fabs(hi) ? fabs(lo) : fabs(hi);
     double err = 2.0 * m * s * (1.0 / 524288.0) + (double)res * (1.0 / 2097152.0);
-    return (err < 0.25 && m < 1e37 && s < 1e37) ? 1 : 0;
+    return (err < 0.25 && m < 1e37 && s < 1e37) ? err : -1.0;
 }
 
 // One block computes the mesh (automatic bounds: from bounds_acc; explicit:
@@ -201,10 +153,14 @@ __global__ void k_grid_setup(GridDesc host_desc, const T* bounds_acc, GridDesc* 
                                                &g.ax[1]);
             g.valid = ok ? 1 : 0;
         }
-        for (int a = 0; a < 2; ++a)
-            g.ax[a].fast = (sizeof(T) == 8 && g.valid)
-                               ? fast_ok(g.ax[a].lo, g.ax[a].hi, g.ax[a].s, g.ax[a].res)
-                               : 0;
+        for (int a = 0; a < 2; ++a) {
+            const double dl = (sizeof(T) == 8 && g.valid)
+                                  ? fast_delta(g.ax[a].lo, g.ax[a].hi, g.ax[a].s, g.ax[a].res)
+                                  : -1.0;
+            g.ax[a].fast = dl >= 0.0 ? 1 : 0;
+            // round the margin up so the float comparison stays conservative
+            g.ax[a].delta = dl >= 0.0 ? __double2float_ru(dl) : 0.0f;
+        }
         g.edges[0] = (sizeof(T) == 8) ? edges0 : nullptr;
         g.edges[1] = (sizeof(T) == 8) ? edges1 : nullptr;
         if (blockIdx.x == 0) {
@@ -378,6 +334,6 @@ cudaError_t launch_gather(const KernelCtx& kc, int dtype, void* dst, const void*
     return cudaGetLastError();
 }
 
-int host_fast_ok(double lo, double hi, double s, int res) { return fast_ok(lo, hi, s, res); }
+double host_fast_delta(double lo, double hi, double s, int res) { return fast_delta(lo, hi, s, res); }
 
 }  // namespace bn

@@ -11,6 +11,7 @@
 // cluster of particles costs one set of atomics per warp, not per lane.
 #include <cuda_runtime.h>
 
+#include "bn_device.cuh"
 #include "bn_internal.cuh"
 #include "bn_kernels.h"
 
@@ -59,80 +60,6 @@ template <> struct GBinner<double> {
     }
 };
 
-// Combine the lanes of the calling warp that share bin b (b >= 0) and let
-// the lowest such lane update the global mesh. Every lane of the warp must
-// call it (b = -1 for lanes without an in-bounds particle).
-template <typename T, int A_CT>
-__device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, const T* v) {
-    const unsigned full = 0xffffffffu;
-    const unsigned peers = __match_any_sync(full, b);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    const bool alone = peers == (1u << lane);
-    if (__all_sync(full, alone || b < 0)) {
-        // no two lanes share a bin: skip the combining shuffles
-        if (b < 0) return;
-        atomicAdd(&st.count[b], 1ull);
-        for (int a = 0; a < A; ++a) {
-            const T x = v[a];
-            if (st.do_sum) atomicAdd(&st.sum[a][b], (double)x);
-            if (is_nan_bits(x)) continue;
-            if (st.do_min) {
-                T* g = static_cast<T*>(st.mn[a]) + b;
-                if (total_less(x, __ldcg(g))) atomic_min_total(g, x);
-            }
-            if (st.do_max) {
-                T* g = static_cast<T*>(st.mx[a]) + b;
-                if (total_less(__ldcg(g), x)) atomic_max_total(g, x);
-            }
-        }
-        return;
-    }
-    // General case: the leader of each peer group gathers its peers' values
-    // lane by lane (the loop runs over the largest group in the warp).
-    const unsigned cnt = __popc(peers);
-    double s[A_CT > 0 ? A_CT : kMaxAttr];
-    T lo[A_CT > 0 ? A_CT : kMaxAttr], hi[A_CT > 0 ? A_CT : kMaxAttr];
-    for (int a = 0; a < A; ++a) {
-        s[a] = 0.0;
-        lo[a] = pos_inf<T>();
-        hi[a] = neg_inf<T>();
-    }
-    unsigned rest = peers;
-    // every lane walks its own group; shuffles need all lanes, so loop to the
-    // warp-wide maximum group size
-    int my_n = (b >= 0) ? (int)cnt : 0;
-    int max_n = my_n;
-    for (int off = 16; off > 0; off >>= 1) max_n = max(max_n, __shfl_xor_sync(full, max_n, off));
-    for (int it = 0; it < max_n; ++it) {
-        int src = rest ? __ffs(rest) - 1 : lane;
-        if (rest) rest &= rest - 1;
-        for (int a = 0; a < A; ++a) {
-            T x = __shfl_sync(full, v[a], src);
-            if (b >= 0 && it < my_n) {
-                s[a] += (double)x;  // FP64 add in this lane's registers
-                if (!is_nan_bits(x)) {
-                    if (total_less(x, lo[a])) lo[a] = x;
-                    if (total_less(hi[a], x)) hi[a] = x;
-                }
-            }
-        }
-    }
-    if (b < 0 || lane != leader) return;
-    atomicAdd(&st.count[b], (unsigned long long)cnt);
-    for (int a = 0; a < A; ++a) {
-        if (st.do_sum) atomicAdd(&st.sum[a][b], s[a]);
-        if (st.do_min && !(lo[a] == pos_inf<T>())) {
-            T* g = static_cast<T*>(st.mn[a]) + b;
-            if (total_less(lo[a], __ldcg(g))) atomic_min_total(g, lo[a]);
-        }
-        if (st.do_max && !(hi[a] == neg_inf<T>())) {
-            T* g = static_cast<T*>(st.mx[a]) + b;
-            if (total_less(__ldcg(g), hi[a])) atomic_max_total(g, hi[a]);
-        }
-    }
-}
-
 template <typename T, int A_CT>
 __global__ void __launch_bounds__(256) k_bin_global(BinArgs args, int64_t head, int64_t groups) {
     using V = typename GVec<T>::type;
@@ -164,7 +91,7 @@ __global__ void __launch_bounds__(256) k_bin_global(BinArgs args, int64_t head, 
                 b = binner.bin(X[i], Y[i]);
                 for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(args.a[a])[i];
             }
-            warp_commit<T, A_CT>(st, A, b, v);
+            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0);
         }
     };
     scalar_range(0, head);
@@ -200,7 +127,7 @@ __global__ void __launch_bounds__(256) k_bin_global(BinArgs args, int64_t head, 
                     for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(args.a[a])[i];
                 }
             }
-            warp_commit<T, A_CT>(st, A, b, v);
+            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0);
         }
     }
 }

@@ -14,185 +14,11 @@
 // exact edge keys, no FP64 arithmetic).
 #include <cuda_runtime.h>
 
+#include "bn_device.cuh"
 #include "bn_internal.cuh"
 #include "bn_kernels.h"
 
 namespace bn {
-
-template <typename T> struct VecOf;
-template <> struct VecOf<float> { using type = float4; static constexpr int N = 4; };
-template <> struct VecOf<double> { using type = double2; static constexpr int N = 2; };
-
-template <typename T>
-__device__ __forceinline__ T vget(const typename VecOf<T>::type& v, int j);
-template <> __device__ __forceinline__ float vget<float>(const float4& v, int j) {
-    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
-}
-template <> __device__ __forceinline__ double vget<double>(const double2& v, int j) {
-    return j == 0 ? v.x : v.y;
-}
-
-// Mesh location of a particle, -1 when outside.
-template <typename T> struct Binner;
-template <> struct Binner<float> {
-    Axis<float> ax, ay;
-    int rx;
-    __device__ void init(const GridDesc& g) {
-        ax = make_axis<float>(g.ax[0]);
-        ay = make_axis<float>(g.ax[1]);
-        rx = g.ax[0].res;
-    }
-    __device__ __forceinline__ int bin(float x, float y) const {
-        int ix = axis_bin(ax, x);
-        int iy = axis_bin(ay, y);
-        return (ix < 0 || iy < 0) ? -1 : iy * rx + ix;
-    }
-};
-template <> struct Binner<double> {
-    AxisF64 ax, ay;
-    int rx;
-    __device__ void init(const GridDesc& g) {
-        ax = make_axis_f64(g.ax[0], g.edges[0]);
-        ay = make_axis_f64(g.ax[1], g.edges[1]);
-        rx = g.ax[0].res;
-    }
-    __device__ __forceinline__ int bin(double x, double y) const {
-        int ix = axis_bin(ax, x);
-        int iy = axis_bin(ay, y);
-        return (ix < 0 || iy < 0) ? -1 : iy * rx + ix;
-    }
-};
-
-// Shared-memory mesh. Sums are FP64 for f64 data and for f32 data in
-// kSumF64 mode; FP32 (plus an FP32 compensation term in kSumF32C) otherwise.
-template <typename T, int MODE>
-struct SmemMesh {
-    static constexpr bool kWide = sizeof(T) == 8 || MODE == kSumF64;
-    unsigned int* cnt;
-    double* s64;
-    float* s32;
-    float* c32;
-    T* mn;
-    T* mx;
-    int B;
-    bool do_sum, do_min, do_max;
-
-    __device__ static size_t bytes(int B, int A, bool do_sum, bool do_min, bool do_max) {
-        size_t b = ((size_t)B * 4 + 15) & ~(size_t)15;
-        if (do_sum) b += (size_t)A * B * (kWide ? 8 : (MODE == kSumF32C ? 8 : 4));
-        if (do_min) b += (size_t)A * B * sizeof(T);
-        if (do_max) b += (size_t)A * B * sizeof(T);
-        return b;
-    }
-
-    __device__ void carve(unsigned char* base, int B_, int A, bool s, bool lo, bool hi) {
-        B = B_;
-        do_sum = s;
-        do_min = lo;
-        do_max = hi;
-        size_t off = ((size_t)B * 4 + 15) & ~(size_t)15;
-        cnt = reinterpret_cast<unsigned int*>(base);
-        s64 = nullptr;
-        s32 = nullptr;
-        c32 = nullptr;
-        if (do_sum) {
-            if (kWide) {
-                s64 = reinterpret_cast<double*>(base + off);
-                off += (size_t)A * B * 8;
-            } else {
-                s32 = reinterpret_cast<float*>(base + off);
-                off += (size_t)A * B * 4;
-                if (MODE == kSumF32C) {
-                    c32 = reinterpret_cast<float*>(base + off);
-                    off += (size_t)A * B * 4;
-                }
-            }
-        }
-        mn = do_min ? reinterpret_cast<T*>(base + off) : nullptr;
-        if (do_min) off += (size_t)A * B * sizeof(T);
-        mx = do_max ? reinterpret_cast<T*>(base + off) : nullptr;
-    }
-
-    __device__ void clear(int A) {
-        for (int b = threadIdx.x; b < B; b += blockDim.x) cnt[b] = 0u;
-        const int AB = A * B;
-        if (do_sum) {
-            if (kWide) {
-                for (int k = threadIdx.x; k < AB; k += blockDim.x) s64[k] = 0.0;
-            } else {
-                for (int k = threadIdx.x; k < AB; k += blockDim.x) s32[k] = 0.0f;
-                if (MODE == kSumF32C)
-                    for (int k = threadIdx.x; k < AB; k += blockDim.x) c32[k] = 0.0f;
-            }
-        }
-        if (do_min)
-            for (int k = threadIdx.x; k < AB; k += blockDim.x) mn[k] = pos_inf<T>();
-        if (do_max)
-            for (int k = threadIdx.x; k < AB; k += blockDim.x) mx[k] = neg_inf<T>();
-    }
-
-    __device__ __forceinline__ void add_count(int b) { atomicAdd(&cnt[b], 1u); }
-
-    __device__ __forceinline__ void add(int a, int b, T v) {
-        const int k = a * B + b;
-        if (do_sum) {
-            if (kWide) {
-                atomicAdd(&s64[k], (double)v);
-            } else if (MODE == kSumF32) {
-                atomicAdd(&s32[k], (float)v);
-            } else {
-                // Two-sum of the value the atomic added to: the exact rounding
-                // error of old + v goes into the compensation term.
-                float fv = (float)v;
-                float old = atomicAdd(&s32[k], fv);
-                float s = __fadd_rn(old, fv);
-                float bp = __fsub_rn(s, old);
-                float err = __fadd_rn(__fsub_rn(old, __fsub_rn(s, bp)), __fsub_rn(fv, bp));
-                // once the sum is +/-inf or NaN the error term is meaningless
-                // (inf - inf); the sum itself already carries the result
-                if (err != 0.0f && (__float_as_uint(err) & 0x7f800000u) != 0x7f800000u)
-                    atomicAdd(&c32[k], err);
-            }
-        }
-        if (is_nan_bits(v)) return;
-        if (do_min && total_less(v, mn[k])) atomic_min_total(&mn[k], v);
-        if (do_max && total_less(mx[k], v)) atomic_max_total(&mx[k], v);
-    }
-
-    // CTA partial -> global mesh, once per non-empty bin.
-    __device__ void merge(const StateDesc& st, int A) {
-        for (int b = threadIdx.x; b < B; b += blockDim.x) {
-            unsigned int c = cnt[b];
-            if (c == 0u) continue;
-            atomicAdd(&st.count[b], (unsigned long long)c);
-            for (int a = 0; a < A; ++a) {
-                const int k = a * B + b;
-                if (do_sum) {
-                    double v;
-                    if (kWide) v = s64[k];
-                    else if (MODE == kSumF32) v = (double)s32[k];
-                    else {
-                        const float hi = s32[k];
-                        v = ((__float_as_uint(hi) & 0x7f800000u) == 0x7f800000u)
-                                ? (double)hi
-                                : __dadd_rn((double)hi, (double)c32[k]);
-                    }
-                    atomicAdd(&st.sum[a][b], v);
-                }
-                if (do_min) {
-                    T m = mn[k];
-                    T* g = static_cast<T*>(st.mn[a]) + b;
-                    if (total_less(m, __ldcg(g))) atomic_min_total(g, m);
-                }
-                if (do_max) {
-                    T m = mx[k];
-                    T* g = static_cast<T*>(st.mx[a]) + b;
-                    if (total_less(__ldcg(g), m)) atomic_max_total(g, m);
-                }
-            }
-        }
-    }
-};
 
 template <typename T, int A_CT, int MODE>
 __global__ void __launch_bounds__(512) k_bin_private(BinArgs args, int64_t head, int64_t groups) {
@@ -325,9 +151,13 @@ static size_t private_bytes_for(int dtype, int mode, int B, int A, bool s, bool 
     const size_t tsz = dtype == BN_F64 ? 8 : 4;
     size_t b = ((size_t)B * 4 + 15) & ~(size_t)15;
     if (s) b += (size_t)A * B * (wide ? 8 : (mode == kSumF32C ? 8 : 4));
-    if (lo) b += (size_t)A * B * tsz;
-    if (hi) b += (size_t)A * B * tsz;
+    b = (b + 15) & ~(size_t)15;
+    if (lo || hi) b += (size_t)A * B * 2 * tsz;  // {min key, max key}
     return b;
+}
+
+size_t private_mesh_bytes(int dtype, int sum_mode, int64_t bins, int n_attrs, bool s, bool lo, bool hi) {
+    return private_bytes_for(dtype, dtype == BN_F64 ? kSumF64 : sum_mode, (int)bins, n_attrs, s, lo, hi);
 }
 
 size_t private_smem_bytes(const BinArgs& a, int smem_optin) {

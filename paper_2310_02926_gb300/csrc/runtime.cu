@@ -126,6 +126,7 @@ extern "C" bn_status bn_context_destroy(bn_context* c) {
     if (!c) return BN_OK;
     DeviceGuard g(c->device);
     cudaStreamSynchronize(c->stream);
+    batch_cache_release(c);
     for (cudaEvent_t ev : c->event_pool) cudaEventDestroy(ev);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     cudaFreeHost(c->status_host);
@@ -336,7 +337,7 @@ static bn_status make_axis_host(double lo, double hi, int res, AxisDesc* d) {
     d->res = res;
     d->closed = 0;
     d->fast = 0;
-    d->pad = 0;
+    d->delta = 0.0f;
     return BN_OK;
 }
 
@@ -519,7 +520,13 @@ int bn::choose_strategy(const BinArgs& a, int smem_optin, int num_sms, uint32_t 
     // Privatise when the mesh fits and there are enough particles per CTA
     // copy of the mesh to amortise clearing and merging it.
     if (smem > 0 && a.n >= 2 * B) return BN_STRATEGY_PRIVATE;
-    (void)num_sms;
+    // Bucketed sort + reduce when the per-tile bucket table stays small next
+    // to the records (few buckets per tile) and there is enough work to
+    // stream; otherwise atomics straight into the global mesh.
+    SortDesc sd;
+    if (sort_plan(a, smem_optin, &sd) && sd.nb * 4 <= sd.tp && a.n >= (int64_t)num_sms * sd.tp &&
+        a.n >= B / 2)
+        return BN_STRATEGY_SORT;
     return BN_STRATEGY_GLOBAL;
 }
 
@@ -541,6 +548,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
     if (st != BN_OK) return st;
     if ((ops & BN_STRATEGY_MASK) > BN_STRATEGY_SORT)
         return fail(BN_ERR_INVALID_ARG, "unknown strategy in ops");
+    if ((ops & BN_AGG_MASK) == BN_AGG_MASK) return fail(BN_ERR_INVALID_ARG, "unknown aggregation mode in ops");
     const uint32_t sum_bits = ops & BN_SUM_MASK;
     if (sum_bits == (3u << 8)) return fail(BN_ERR_INVALID_ARG, "unknown sum mode in ops");
 
@@ -568,6 +576,11 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
                     : sum_bits == BN_SUM_F64 ? kSumF64
                                              : kSumF32C;
     args.n = n;
+    // warp aggregation: on request, else for meshes small enough that a warp
+    // of random particles often shares bins (clustered data raises that)
+    const uint32_t agg = ops & BN_AGG_MASK;
+    args.aggregate = agg == BN_AGG_ON ? 1 : agg == BN_AGG_OFF ? 0
+                     : ((int64_t)grid->res[0] * grid->res[1] <= 65536 ? 1 : 0);
     st = plan.column(x, dtype, &args.x);
     if (st == BN_OK) st = plan.column(y, dtype, &args.y);
     for (int a = 0; a < n_attrs && st == BN_OK; ++a) st = plan.column(&attrs[a], dtype, &args.a[a]);
@@ -647,14 +660,23 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
     args.grid = gd;
     if (n > 0) {
         int strat = choose_strategy(args, c->smem_optin, c->num_sms, ops);
-        if (strat == BN_STRATEGY_SORT) strat = BN_STRATEGY_GLOBAL;
         if (strat == BN_STRATEGY_PRIVATE && private_smem_bytes(args, c->smem_optin) == 0)
             return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_PRIVATE: the mesh does not fit in shared memory");
+        SortDesc sd;
+        void* sort_scratch = nullptr;
+        if (strat == BN_STRATEGY_SORT) {
+            if (!sort_plan(args, c->smem_optin, &sd))
+                return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_SORT: the mesh has too many buckets for the sort path");
+            sort_scratch = plan.alloc(sort_scratch_bytes(sd, args));
+            if (!sort_scratch) return cuda_fail(plan.err, "cudaMallocAsync(sort scratch)");
+        }
         plan.strategy = strat;
         cudaEvent_t t0 = nullptr, t1 = nullptr;
         if (c->profile && cudaEventCreate(&t0) == cudaSuccess && cudaEventCreate(&t1) == cudaSuccess)
             cudaEventRecord(t0, plan.stream);
-        e = strat == BN_STRATEGY_PRIVATE ? launch_bin_private(kc, args) : launch_bin_global(kc, args);
+        e = strat == BN_STRATEGY_PRIVATE ? launch_bin_private(kc, args)
+            : strat == BN_STRATEGY_SORT  ? launch_bin_sort(kc, args, sd, sort_scratch)
+                                         : launch_bin_global(kc, args);
         if (t1) {
             cudaEventRecord(t1, plan.stream);
             std::lock_guard<std::mutex> lk(c->prof_mu);

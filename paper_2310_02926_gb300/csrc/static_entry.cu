@@ -170,6 +170,7 @@ extern "C" bn_status bn_bin_particles_static(const bn_buffer* x, const bn_buffer
     const uint32_t sum_bits = ops & BN_SUM_MASK;
     args.sum_mode = dtype == BN_F64 ? kSumF64 : sum_bits == BN_SUM_F32 ? kSumF32
                                               : sum_bits == BN_SUM_F64 ? kSumF64 : kSumF32C;
+    args.aggregate = B <= 65536 ? 1 : 0;
     args.x = x->ptr;
     args.y = y->ptr;
     for (int a = 0; a < n_attrs; ++a) args.a[a] = attrs[a].ptr;
@@ -187,6 +188,8 @@ extern "C" bn_status bn_bin_particles_static(const bn_buffer* x, const bn_buffer
         e = launch_grid_setup(kc, dtype, gd, bounds_acc, dev_grid, dtype == BN_F64 ? e0 : nullptr,
                               dtype == BN_F64 ? e1 : nullptr, bounds_out, status);
     if (e == cudaSuccess && n > 0) {
+        // the sort path needs a large scratch area, so this entry point
+        // chooses only between the shared-memory and the global-atomic paths
         int strat = choose_strategy(args, optin, sms, ops);
         e = strat == BN_STRATEGY_PRIVATE ? launch_bin_private(kc, args) : launch_bin_global(kc, args);
     }

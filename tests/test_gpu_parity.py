@@ -51,12 +51,34 @@ def test_uniform64_f64_config(bn, ctx, strategy):
     check(w, run_gpu(ctx, w, flags=flags), TOL_F64, label=strategy)
 
 
-@pytest.mark.parametrize("strategy", ["auto", "global"])
+STRAT = {"auto": 0, "private": "STRATEGY_PRIVATE", "global": "STRATEGY_GLOBAL", "sort": "STRATEGY_SORT"}
+
+
+def sflag(bn, name):
+    v = STRAT[name]
+    return v if isinstance(v, int) else getattr(bn, v)
+
+
+@pytest.mark.parametrize("strategy", ["auto", "global", "sort"])
 def test_plummer_f64_reduced(bn, ctx, strategy):
     """Plummer sphere projected on x-y, 3 f64 attributes, 1024x1024 over [-10,10]^2."""
     w = workloads.plummer(2_000_003, seed=1, dtype=np.float64, res=1024)
-    flags = {"auto": 0, "global": bn.STRATEGY_GLOBAL}[strategy]
+    flags = sflag(bn, strategy)
     check(w, run_gpu(ctx, w, flags=flags), TOL_F64, label=strategy)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_sort_splits_dense_bucket_across_items(bn, ctx, dtype):
+    """300,000 particles in one bin and 100,000 spread out: the dense bucket
+    holds more records than one work item, so its items merge atomically."""
+    rng = np.random.default_rng(31)
+    n1, n2 = 300_000, 100_000
+    x = np.concatenate([np.full(n1, 0.3141), rng.random(n2)]).astype(dtype)
+    y = np.concatenate([np.full(n1, 0.2718), rng.random(n2)]).astype(dtype)
+    p = rng.permutation(n1 + n2)
+    a = [rng.normal(0, 1, n1 + n2).astype(dtype)[p], rng.uniform(-5, 5, n1 + n2).astype(dtype)[p]]
+    w = workloads.Workload("dense", x[p], y[p], a, (0.0, 0.0), (1.0, 1.0), (600, 500))
+    check(w, run_gpu(ctx, w, flags=bn.STRATEGY_SORT), TOL_F64 if dtype == np.float64 else TOL_F32C)
 
 
 def test_private_rejects_mesh_too_large_for_shared_memory(bn, ctx):
@@ -66,17 +88,18 @@ def test_private_rejects_mesh_too_large_for_shared_memory(bn, ctx):
     assert e.value.code == bn.ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("res,strategy", [(1024, "global"), (64, "private"), (128, "global")])
+@pytest.mark.parametrize("res,strategy", [(1024, "global"), (64, "private"), (128, "global"),
+                                          (1024, "sort"), (128, "sort")])
 @pytest.mark.parametrize("mode", ["f32c", "f32", "f64"])
 def test_gaussians_f32_sum_modes(bn, ctx, res, strategy, mode):
     """16-Gaussian mixture, f32 columns; the three sum modes against the FP64 oracle."""
     w = workloads.gaussians(2 ** 21 + 13, seed=3, res=res)
     flags = {"f32c": bn.SUM_F32C, "f32": bn.SUM_F32, "f64": bn.SUM_F64}[mode]
-    flags |= {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    flags |= sflag(bn, strategy)
     gpu = run_gpu(ctx, w, flags=flags)
     ref = oracle.bin_workload(w)
     sabs = abs_sums(w)
-    if mode == "f32" and strategy == "private":
+    if mode == "f32" and strategy in ("private", "sort"):
         # plain FP32 partials: exact counts/min/max; sums bounded by the
         # number of terms a CTA adds into one bin times 2^-24
         assert_parity(gpu, ref, sabs, 1.0, label=mode)
@@ -89,17 +112,17 @@ def test_gaussians_f32_sum_modes(bn, ctx, res, strategy, mode):
 
 # ------------------------------------------------------------------ edge cases
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("strategy", ["private", "global"])
-@pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 31, 33, 1023, 1025, 70_001])
+@pytest.mark.parametrize("strategy", ["private", "global", "sort"])
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 31, 33, 1023, 1025, 4095, 4097, 70_001])
 def test_ragged_lengths(bn, ctx, dtype, strategy, n):
     w = workloads.uniform(n, seed=4 + n, dtype=dtype, res=16)
-    flags = {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    flags = sflag(bn, strategy)
     check(w, run_gpu(ctx, w, flags=flags), TOL_F64 if dtype == np.float64 else TOL_F32C,
           label=f"n={n}")
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("strategy", ["private", "global"])
+@pytest.mark.parametrize("strategy", ["private", "global", "sort"])
 @pytest.mark.parametrize("offsets", [(1, 1, 1, 1), (1, 2, 3, 0), (3, 3, 3, 3)])
 def test_misaligned_columns(bn, ctx, dtype, strategy, offsets):
     """Sub-range views whose starts are not 16-byte aligned (same or mixed phase)."""
@@ -110,7 +133,7 @@ def test_misaligned_columns(bn, ctx, dtype, strategy, offsets):
     cols = [t[o:o + n] for t, o in zip(full, offsets)]
     host = [np.ascontiguousarray(c[o:o + n]) for c, o in zip((w.x, w.y, *w.attrs), offsets)]
     wv = workloads.Workload("view", host[0], host[1], host[2:], w.lo, w.hi, w.res)
-    flags = {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    flags = sflag(bn, strategy)
     out = ctx.bin_particles(cols[0], cols[1], cols[2:], w.lo, w.hi, w.res, ops=bn.OP_ALL | flags)
     torch.cuda.synchronize()
     check(wv, to_numpy_result(out), TOL_F64 if dtype == np.float64 else TOL_F32C)
@@ -128,7 +151,7 @@ def test_strided_columns(bn, ctx, dtype):
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("strategy", ["private", "global"])
+@pytest.mark.parametrize("strategy", ["private", "global", "sort"])
 def test_special_values(bn, ctx, dtype, strategy):
     rng = np.random.default_rng(7)
     n = 20_000
@@ -149,7 +172,7 @@ def test_special_values(bn, ctx, dtype, strategy):
     b[::67] = np.inf
     b[1::71] = -np.inf
     w = workloads.Workload("special", x, y, [a, b], (0.0, 0.0), (1.0, 1.0), (8, 8))
-    flags = {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    flags = sflag(bn, strategy)
     check(w, run_gpu(ctx, w, flags=flags), TOL_F64 if dtype == np.float64 else TOL_F32C)
 
 
@@ -163,7 +186,7 @@ F64_GRIDS = [
 
 
 @pytest.mark.parametrize("grid", F64_GRIDS)
-@pytest.mark.parametrize("strategy", ["private", "global"])
+@pytest.mark.parametrize("strategy", ["private", "global", "sort"])
 def test_f64_bin_edges_exact(bn, ctx, grid, strategy):
     """Particles on and within a few ulp of every bin edge: indices must
     follow the round-to-nearest sequence exactly (via the edge-key method)."""
@@ -189,16 +212,16 @@ def test_f64_bin_edges_exact(bn, ctx, grid, strategy):
         (x if a == 0 else y)[k] = v
     m = rng.uniform(1, 2, n)
     w = workloads.Workload("edges", x, y, [m], lo, hi, res)
-    flags = {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    flags = sflag(bn, strategy)
     check(w, run_gpu(ctx, w, flags=flags), TOL_F64)
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("strategy", ["private", "global"])
+@pytest.mark.parametrize("strategy", ["private", "global", "sort"])
 def test_auto_bounds(bn, ctx, dtype, strategy):
     w = workloads.plummer(300_001, seed=9, dtype=dtype, res=40)
     w.x[::1000] = np.nan
-    flags = {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    flags = sflag(bn, strategy)
     gpu = run_gpu(ctx, w, flags=flags, auto_bounds=True, bounds=True)
     (_, ref) = check(w, gpu, TOL_F64 if dtype == np.float64 else TOL_F32C, auto_bounds=True)
     assert gpu["bounds"].tolist() == ref["bounds"].tolist()
@@ -311,6 +334,56 @@ def test_batch_of_uneven_blocks(bn, ctx):
         keep += [cols, r]
         outs.append((w, o))
         blocks.append(bn.block(cols[0], cols[1], cols[2:], bn.grid(w.lo, w.hi, w.res), r))
+    bn.bn_bin_batch(ctx.handle, blocks, bn.OP_ALL)
+    torch.cuda.synchronize()
+    for w, o in outs:
+        check(w, to_numpy_result(o), TOL_F32C, label=w.name)
+
+
+def _batch_blocks(bn, plan, dtype, host=False, scale=None):
+    import torch as T
+    blocks, outs, keep = [], [], []
+    for k in range(plan.n_blocks):
+        w = plan.block(k)
+        if scale is not None:
+            w.attrs = [a * scale for a in w.attrs]
+        w.x, w.y = w.x.astype(dtype), w.y.astype(dtype)
+        w.attrs = [a.astype(dtype) for a in w.attrs]
+        dev = T.device("cpu") if host else T.device("cuda")
+        cols = [T.from_numpy(np.ascontiguousarray(c)).to(dev) for c in (w.x, w.y, *w.attrs)]
+        o = bn.alloc_outputs(2, w.res[0] * w.res[1], cols[0].dtype, T.device("cuda"))
+        r = bn.result_struct(o)
+        keep += [cols, r]
+        outs.append((w, o))
+        blocks.append(bn.block(cols[0], cols[1], cols[2:], bn.grid(w.lo, w.hi, w.res), r))
+    return blocks, outs, keep
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("strategy", ["auto", "private", "global"])
+def test_batch_persistent_path(bn, ctx, dtype, strategy):
+    """All-device batch: one persistent launch (graph-captured), every block
+    checked against the oracle; then the same shapes with new values replay
+    the cached graph."""
+    plan = workloads.batch(n_blocks=20, seed=41, size_range=(1e3, 3e5),
+                           side_range=(8, 40 if strategy == "private" else 700))
+    tol = TOL_F64 if dtype == np.float64 else TOL_F32C
+    flags = {"auto": 0, "private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL}[strategy]
+    for rep, scale in enumerate((None, -3.0)):
+        blocks, outs, keep = _batch_blocks(bn, plan, dtype, scale=scale)
+        launches0 = ctx.launches
+        bn.bn_bin_batch(ctx.handle, blocks, bn.OP_ALL | flags)
+        torch.cuda.synchronize()
+        if rep == 1:
+            # a replay of the captured graph: init/edges, persistent pass, finalize
+            assert ctx.launches - launches0 <= 4
+        for w, o in outs:
+            check(w, to_numpy_result(o), tol, label=f"{w.name} rep{rep}")
+
+
+def test_batch_general_path_with_host_columns(bn, ctx):
+    plan = workloads.batch(n_blocks=5, seed=42, size_range=(1e3, 5e4), side_range=(8, 200))
+    blocks, outs, keep = _batch_blocks(bn, plan, np.float32, host=True)
     bn.bn_bin_batch(ctx.handle, blocks, bn.OP_ALL)
     torch.cuda.synchronize()
     for w, o in outs:
