@@ -56,6 +56,13 @@ WORKLOADS = {
     "gaussians4096": ("gaussians", 2 ** 27, 4096, 2, "f32",
                       "16-Gaussian mixture in [0,1)^2, {n:,} f32 particles, 2 f32 attributes "
                       "U[0,1e4], 4096x4096 mesh, count/sum/min/max/avg"),
+    "batch256": ("batch", 256, 0, 2, "f32",
+                 "{n} blocks of log-uniform 1e3..1e7 f32 particles (uniform or Plummer per block), "
+                 "square meshes log-uniform 32..2048, 2 attributes, one bn_bin_batch call"),
+    "serving": ("serving", 10_000, 0, 3, "f32",
+                "Poisson stream of {n:,} requests (mean 2 ms apart, log-uniform 1e4..2e7 f32 "
+                "particles, meshes 64^2..1024^2) under a 40 GB budget beside a direct-sum "
+                "gravity producer (N=65,536 f32)"),
 }
 # kernel sources whose ncu traffic record applies, per particle-pass strategy
 KERNEL_SOURCES = {
@@ -230,6 +237,249 @@ def run_reference(args):
     return 0
 
 
+def compare_with_oracle(w, out, bn):
+    """Per-bin error of the GPU result against the CPU oracle: counts, min
+    and max must match exactly; for sums, |gpu - oracle| / sum|a| over
+    non-empty bins (max and 99th percentile)."""
+    import numpy as np
+    import oracle
+    ref = oracle.bin_workload(w)
+    sabs = oracle.bin_particles(w.x, w.y, [np.abs(a) for a in w.attrs], w.lo, w.hi, w.res)["sum"]
+    cnt = out["count"].cpu().numpy().astype(np.uint64)
+    res = {"count_exact": bool(np.array_equal(cnt, ref["count"]))}
+    ne = ref["count"] > 0
+    rel_all = []
+    for a in range(len(w.attrs)):
+        g = out["sum"][a].cpu().numpy()
+        mn = out["min"][a].cpu().numpy()
+        mx = out["max"][a].cpu().numpy()
+        res[f"min{a}_exact"] = bool(np.array_equal(mn.view(np.int64 if mn.itemsize == 8 else np.int32),
+                                                   ref["min"][a].view(np.int64 if mn.itemsize == 8 else np.int32)))
+        res[f"max{a}_exact"] = bool(np.array_equal(mx.view(np.int64 if mx.itemsize == 8 else np.int32),
+                                                   ref["max"][a].view(np.int64 if mx.itemsize == 8 else np.int32)))
+        rel = np.abs(g[ne] - ref["sum"][a][ne]) / sabs[a][ne]
+        rel_all.append(rel)
+    rel = np.concatenate(rel_all) if rel_all else np.zeros(1)
+    res["sum_rel_err_max"] = float(rel.max())
+    res["sum_rel_err_p99"] = float(np.percentile(rel, 99))
+    res["bins_checked"] = int(ne.sum())
+    return res
+
+
+def run_batch(args, n_blocks):
+    """Batching: every block of the plan binned in one bn_bin_batch call
+    (f32 columns, compensated FP32 sums), against the same blocks in f64
+    binned one bn_bin_particles call after another (the plain FP64 form)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2310_02926_gb300 as bn
+    import workloads
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    plan = workloads.batch(n_blocks=n_blocks, seed=0)
+    ctx = bn.Context(0, stream=stream.cuda_stream)
+    blocks32, keep, outs64, cols64 = [], [], [], []
+    total = 0
+    t0 = time.time()
+    with torch.cuda.stream(stream):
+        for k in range(plan.n_blocks):
+            w = plan.block(k)
+            total += w.n
+            c32 = [torch.from_numpy(c).to(dev) for c in (w.x, w.y, *w.attrs)]
+            o32 = bn.alloc_outputs(2, w.res[0] * w.res[1], torch.float32, dev)
+            r32 = bn.result_struct(o32)
+            keep.append((c32, o32, r32))
+            blocks32.append(bn.block(c32[0], c32[1], c32[2:], bn.grid(w.lo, w.hi, w.res), r32))
+            c64 = [c.double() for c in c32]
+            o64 = bn.alloc_outputs(2, w.res[0] * w.res[1], torch.float64, dev)
+            cols64.append((c64, bn.grid(w.lo, w.hi, w.res), bn.result_struct(o64), o64))
+        gen_s = time.time() - t0
+        ops = bn.OP_ALL | bn.SUM_F32C
+
+        def timed(fn, steps, warm):
+            reqs = []
+            for _ in range(warm):
+                fn()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = ctx.launches
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / steps, (ctx.launches - l0) // steps
+
+        # request handles of asynchronous calls are freed as they complete
+        def batched():
+            r = bn.bn_bin_batch(ctx.handle, blocks32, ops, sync=False)
+            bn.bn_request_release(r)
+
+        def plain():
+            for c64, g, r, _ in cols64:
+                q = bn.bn_bin_particles(ctx.handle, c64[0], c64[1], c64[2:], g, bn.OP_ALL, r, sync=False)
+                bn.bn_request_release(q)
+
+        ms_b, launches_b = timed(batched, args.steps, args.warmup)
+        ms_p, launches_p = timed(plain, max(1, args.steps // 4), 1)
+    bytes32 = total * 16
+    hbm, peak_src = peaks()
+    line = {"metric": METRIC, "value": total / (ms_b / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS["batch256"][5].format(n=plan.n_blocks),
+                       "name": "batch256", "n_particles": total, "n_blocks": plan.n_blocks,
+                       "sum_mode": "f32c", "l2": "inputs 4+ GB > L2"},
+            "batched_fp32": {"particles_per_s": total / (ms_b / 1e3), "ms": ms_b,
+                             "hbm_frac_read": bytes32 / (ms_b / 1e3) / 1e9 / hbm,
+                             "gpu_launches_per_step": launches_b},
+            "plain_fp64": {"particles_per_s": total / (ms_p / 1e3), "ms": ms_p,
+                           "gpu_launches_per_step": launches_p},
+            "speedup_batched_fp32_vs_plain_fp64": ms_p / ms_b,
+            "data_generation_s": gen_s}
+    if args.check:
+        worst = 0.0
+        exact = True
+        for k in range(plan.n_blocks):
+            w = plan.block(k)
+            o = {kk: vv for kk, vv in keep[k][1].items()}
+            e = compare_with_oracle(w, o, bn)
+            worst = max(worst, e["sum_rel_err_max"])
+            exact = exact and e["count_exact"] and all(v for kk, v in e.items() if kk.endswith("_exact"))
+        line["errors_vs_oracle"] = {"exact_count_min_max": exact, "sum_rel_err_max": worst}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_serving(args, n_requests):
+    """Serving: a Poisson stream of requests submitted to a bn_server at
+    their arrival times while the n-body producer runs on its own stream;
+    latency is arrival -> completion seen by the submitting thread."""
+    import ctypes
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2310_02926_gb300 as bn
+    import workloads
+    dev = torch.device("cuda", 0)
+    plan = workloads.serving(n_requests=n_requests, seed=0)
+    pool = [torch.from_numpy(c).to(dev) for c in (plan.pool.x, plan.pool.y, *plan.pool.attrs)]
+    ctx = bn.Context(0)
+    try:
+        lo_prio, hi_prio = torch.cuda.Stream.priority_range()
+    except Exception:
+        lo_prio, hi_prio = 0, -1
+    prio = hi_prio if args.serving_priority == "high" else lo_prio
+    srv = bn.bn_server_create(ctx.handle, 40 << 30, max_inflight=4, max_batch=32, priority=prio)
+    # output slots, reused once their request has completed
+    max_side = int(plan.sides.max())
+    n_slots = 128
+    slots = [bn.alloc_outputs(3, max_side * max_side, torch.float32, dev) for _ in range(n_slots)]
+    free = list(range(n_slots))
+    # producer: direct-sum gravity, N = 65,536, its own stream
+    prod_stream = torch.cuda.Stream(device=dev)
+    g = torch.Generator().manual_seed(1)
+    nb = 65_536
+    pos = torch.zeros(nb, 4)
+    pos[:, :3] = torch.randn(nb, 3, generator=g)
+    pos[:, 3] = 1.0 / nb
+    pos, vel, acc = pos.to(dev), torch.zeros(nb, 4, device=dev), torch.zeros(nb, 4, device=dev)
+    acc_ok = ctypes.c_int(0)
+    stop = threading.Event()
+    prod_times = []
+
+    def producer():
+        torch.cuda.set_device(dev)
+        evs = []
+        while not stop.is_set():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(prod_stream)
+            bn.bn_nbody_step(pos, vel, acc, acc_ok, 1e-3, 1e-3, prod_stream.cuda_stream)
+            e1.record(prod_stream)
+            evs.append((e0, e1))
+            if len(evs) > 2:
+                a, b = evs.pop(0)
+                b.synchronize()
+                prod_times.append(a.elapsed_time(b))
+
+    def producer_alone(seconds):
+        th = threading.Thread(target=producer)
+        th.start()
+        time.sleep(seconds)
+        stop.set()
+        th.join()
+        stop.clear()
+        t = list(prod_times)
+        prod_times.clear()
+        return t
+
+    alone = producer_alone(2.0) if not args.no_producer else []
+    th = threading.Thread(target=producer)
+    if not args.no_producer:
+        th.start()
+        time.sleep(0.5)
+    prod_times.clear()
+    lat, outstanding, served = [], [], 0
+    t_start = time.perf_counter()
+    i = 0
+    while i < plan.n_requests or outstanding:
+        now = time.perf_counter() - t_start
+        while i < plan.n_requests and plan.arrival_s[i] <= now and free:
+            o0, n, side = int(plan.offsets[i]), int(plan.sizes[i]), int(plan.sides[i])
+            sl = free.pop()
+            o = {k: (v[:side * side] if not isinstance(v, list) else [t[:side * side] for t in v])
+                 for k, v in slots[sl].items()}
+            r = bn.result_struct(o, stream=0)
+            blk = bn.block(*[c[o0:o0 + n] for c in pool[:2]], [c[o0:o0 + n] for c in pool[2:]],
+                           bn.grid((-10, -10), (10, 10), (side, side)), r, stream=0)
+            req = bn.bn_server_submit(srv, blk, bn.OP_ALL)
+            outstanding.append((req, plan.arrival_s[i], n, sl, r, blk))
+            i += 1
+        keep = []
+        now = time.perf_counter() - t_start
+        for item in outstanding:
+            st = bn.lib().bn_query(item[0])
+            if st == bn.NOT_READY:
+                keep.append(item)
+                continue
+            if st < 0:
+                raise RuntimeError(f"request failed: {st}")
+            lat.append(now - item[1])
+            served += item[2]
+            free.append(item[3])
+            bn.bn_request_release(item[0])
+        outstanding = keep
+    wall = time.perf_counter() - t_start
+    stop.set()
+    if not args.no_producer:
+        th.join()
+    with_serving = list(prod_times)
+    stats = bn.bn_server_stats_get(srv)
+    bn.bn_server_destroy(srv)
+    ctx.close()
+    lat_ms = np.array(lat) * 1e3
+    line = {"metric": METRIC, "value": served / wall, "unit": UNIT, "n_gpus": 1,
+            "steps": plan.n_requests, "warmup": 0, "ms_per_step": wall * 1e3 / plan.n_requests,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS["serving"][5].format(n=plan.n_requests),
+                       "name": "serving", "budget_gb": 40, "max_inflight": 4, "max_batch": 32,
+                       "server_priority": args.serving_priority, "producer": not args.no_producer},
+            "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                           "max": float(lat_ms.max()), "mean": float(lat_ms.mean())},
+            "particles_served": int(served), "wall_s": wall,
+            "producer_step_ms": {"alone": float(np.median(alone)) if alone else None,
+                                 "with_serving": float(np.median(with_serving)) if with_serving else None},
+            "server": stats}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     global N_PART
     ap = argparse.ArgumentParser()
@@ -246,12 +496,21 @@ def main():
                     help="particles (0 = the workload's size; smaller cases for profiling runs)")
     ap.add_argument("--sum", default="f32c", choices=["f32c", "f32", "f64"],
                     help="sum mode for f32 workloads")
+    ap.add_argument("--serving-priority", default="high", choices=["low", "high"],
+                    help="stream priority of the server relative to the producer")
+    ap.add_argument("--no-producer", action="store_true", help="serving without the producer")
+    ap.add_argument("--check", action="store_true",
+                    help="compare the last step with the CPU oracle and report per-bin errors")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
     N_PART = args.n or WORKLOADS[args.workload][1]
+    if args.workload == "batch256":
+        return run_batch(args, N_PART)
+    if args.workload == "serving":
+        return run_serving(args, N_PART)
 
     import numpy as np
     import torch
@@ -354,6 +613,10 @@ def main():
         e2e = {"value": N_PART / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_in,
                "d2h_bytes_per_step": bytes_out, "ms_per_step": 1e3 * t_e2e}
 
+    errors = None
+    if args.check and rank == 0:
+        errors = compare_with_oracle(w, out, bn)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, reps, secs = time_oracle(w, min_seconds=10.0, max_reps=4)
@@ -381,6 +644,8 @@ def main():
             "gpu_launches": gpu_launches,
             "clocks": clk,
         }
+        if errors is not None:
+            line["errors_vs_oracle"] = errors
         print(json.dumps(line), flush=True)
     ctx.close()
     if pg:

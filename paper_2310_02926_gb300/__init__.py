@@ -255,17 +255,28 @@ def bn_server_destroy(srv: int) -> None:
     check(lib().bn_server_destroy(srv))
 
 
+def bn_nbody_step(pos, vel, acc, state: ctypes.c_int, dt: float, eps: float,
+                  stream: Optional[int] = None) -> None:
+    """One leapfrog step of the direct-sum gravity producer (harness, not
+    binning). pos/vel/acc: CUDA float32 tensors of shape (n, 4)."""
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream(pos.device).cuda_stream
+    check(lib().bn_nbody_step(pos.data_ptr(), vel.data_ptr(), acc.data_ptr(), ctypes.byref(state),
+                              pos.shape[0], dt, eps, s))
+
+
 def bn_version() -> str:
     return lib().bn_version().decode()
 
 
-def block(x, y, attrs: Sequence, g: bn_grid, out: bn_result) -> bn_block:
-    """A bn_block over torch tensors; keep `out` alive while it is in use."""
+def block(x, y, attrs: Sequence, g: bn_grid, out: bn_result, stream: Optional[int] = None) -> bn_block:
+    """A bn_block over torch tensors; keep `out` alive while it is in use.
+    stream: owning stream of the columns (default: torch's current stream)."""
     b = bn_block()
-    b.x = buffer(x)
-    b.y = buffer(y)
+    b.x = buffer(x, stream)
+    b.y = buffer(y, stream)
     for a, t in enumerate(attrs):
-        b.attrs[a] = buffer(t)
+        b.attrs[a] = buffer(t, stream)
     b.n_attrs = len(attrs)
     b.grid = g
     b.out = ctypes.pointer(out)

@@ -133,17 +133,25 @@ PROTOTYPES = {
     "bn_server_submit": (S, [P, ctypes.POINTER(bn_block), ctypes.c_uint32, PP]),
     "bn_server_stats_get": (S, [P, ctypes.POINTER(bn_server_stats)]),
     "bn_server_destroy": (S, [P]),
+    "bn_nbody_step": (S, [P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.c_int64, ctypes.c_float,
+                          ctypes.c_float, P]),
     "bn_last_error": (ctypes.c_char_p, []),
     "bn_version": (ctypes.c_char_p, []),
 }
 
 
 def header_entry_points(path: str) -> list:
-    """Names of the entry points declared in include/binning.h."""
+    """Names of the entry points declared in a header (or every header of a
+    directory) under include/."""
+    import glob
     import re
-    with open(path) as f:
-        src = f.read()
-    return sorted(set(re.findall(r"^BN_API\s+[\w\s\*]+?\b(bn_\w+)\s*\(", src, flags=re.M)))
+    paths = sorted(glob.glob(os.path.join(path, "*.h"))) if os.path.isdir(path) else [path]
+    names = set()
+    for p in paths:
+        with open(p) as f:
+            src = f.read()
+        names.update(re.findall(r"^BN_API\s+[\w\s\*]+?\b(bn_\w+)\s*\(", src, flags=re.M))
+    return sorted(names)
 
 
 def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
@@ -154,5 +162,5 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     return lib
 
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                      "include", "binning.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+HEADER = os.path.join(INCLUDE, "binning.h")

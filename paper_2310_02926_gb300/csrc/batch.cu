@@ -482,8 +482,6 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
         // same shape: wait until the pinned descriptors are free, rewrite them
         cudaEventSynchronize(G->last);
         unsigned char* host = static_cast<unsigned char*>(G->host);
-        int4* unused_items = nullptr;
-        (void)unused_items;
         int64_t edge_off = 0;
         for (int k = 0; k < n_blocks; ++k) {
             FastBlock& f = fbs[k];

@@ -57,6 +57,7 @@ struct SortDesc {
     int log2bk;        // bins per bucket = 1 << log2bk
     int nb;            // buckets
     int tp;            // particles per pass-1 tile
+    int per;           // particles per pass-1 thread (tp / per threads)
     int chunk;         // records per pass-2 work item (about)
     int64_t tiles;     // pass-1 tiles
     int64_t slots;     // tiles * tp record slots

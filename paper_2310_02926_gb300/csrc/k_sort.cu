@@ -59,16 +59,16 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int* 
 }
 
 // ------------------------------------------------------------------ pass 1
-// One tile of TP = 8 * blockDim particles per CTA. Coordinates are loaded
+// One tile of TP = PER * blockDim particles per CTA. Coordinates are loaded
 // first (8 per thread, coalesced), each particle's bucket rank is taken with
 // a shared-memory atomic, the bucket counts are scanned, and then the
 // attributes are loaded and written straight to their sorted slot in shared
 // memory, so registers hold only (bucket, local bin, rank) per particle and
 // two CTAs fit on an SM.
-template <typename T, int A_CT>
-__global__ void __launch_bounds__(512, 2) k_sort_scatter(BinArgs args, SortDesc sd) {
+template <typename T, int A_CT, int PER>
+__global__ void __launch_bounds__(512) k_sort_scatter(BinArgs args, SortDesc sd) {
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int PER = 8;  // particles per thread (TP = 8 * blockDim)
+    // PER particles per thread: TP = PER * blockDim
     const GridDesc g = args.dev_grid ? *args.dev_grid : args.grid;
     if (!g.valid) return;
     const int A = A_CT >= 0 ? A_CT : args.n_attrs;
@@ -90,31 +90,37 @@ __global__ void __launch_bounds__(512, 2) k_sort_scatter(BinArgs args, SortDesc 
 
     const T* __restrict__ X = static_cast<const T*>(args.x);
     const T* __restrict__ Y = static_cast<const T*>(args.y);
-    int bucket[PER], slot[PER];  // slot = local bin | rank << 16, before the scan
+    int bucket[PER], slot[PER];  // slot = local bin | rank << 16, then the sorted position
     {
-        T xv[PER], yv[PER];
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int64_t p = base + j * blockDim.x + threadIdx.x;
-            xv[j] = p < n ? __ldcs(X + p) : T(0);
-            yv[j] = p < n ? __ldcs(Y + p) : T(0);
-        }
         const int lane = threadIdx.x & 31;
         const unsigned lt = (1u << lane) - 1u;
+        // coordinates in groups of 8 per thread, so only the bucket and slot
+        // of each particle stay in registers
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int64_t p = base + j * blockDim.x + threadIdx.x;
-            const int b = p < n ? binner.bin(xv[j], yv[j]) : -1;
-            bucket[j] = b < 0 ? -1 : (b >> sd.log2bk);
-            // one shared atomic per distinct bucket in the warp: the lowest
-            // lane of each group reserves the group's ranks
-            const unsigned peers = __match_any_sync(0xffffffffu, bucket[j]);
-            const int leader = __ffs(peers) - 1;
-            int r0 = 0;
-            if (lane == leader && bucket[j] >= 0) r0 = atomicAdd(&hist[bucket[j]], __popc(peers));
-            r0 = __shfl_sync(0xffffffffu, r0, leader);
-            const int r = r0 + __popc(peers & lt);
-            slot[j] = (b & ((1 << sd.log2bk) - 1)) | (r << 16);
+        for (int j0 = 0; j0 < PER; j0 += 8) {
+            T xv[8], yv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t p = base + (j0 + u) * blockDim.x + threadIdx.x;
+                xv[u] = p < n ? __ldcs(X + p) : T(0);
+                yv[u] = p < n ? __ldcs(Y + p) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u;
+                const int64_t p = base + j * blockDim.x + threadIdx.x;
+                const int b = p < n ? binner.bin(xv[u], yv[u]) : -1;
+                bucket[j] = b < 0 ? -1 : (b >> sd.log2bk);
+                // one shared atomic per distinct bucket in the warp: the lowest
+                // lane of each group reserves the group's ranks
+                const unsigned peers = __match_any_sync(0xffffffffu, bucket[j]);
+                const int leader = __ffs(peers) - 1;
+                int r0 = 0;
+                if (lane == leader && bucket[j] >= 0) r0 = atomicAdd(&hist[bucket[j]], __popc(peers));
+                r0 = __shfl_sync(0xffffffffu, r0, leader);
+                const int r = r0 + __popc(peers & lt);
+                slot[j] = (b & ((1 << sd.log2bk) - 1)) | (r << 16);
+            }
         }
     }
     __syncthreads();
@@ -143,24 +149,28 @@ __global__ void __launch_bounds__(512, 2) k_sort_scatter(BinArgs args, SortDesc 
             if (c) atomicAdd(&sd.bucket_total[k], c);
         }
     }
-    // sorted position of each particle; keys now, attributes column by column
-    int pos[PER];
+    // sorted position of each particle (reusing slot); keys now, attributes
+    // column by column in groups of 8
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
-        pos[j] = bucket[j] < 0 ? -1 : hist[bucket[j]] + (slot[j] >> 16);
-        if (pos[j] >= 0) skey[pos[j]] = (unsigned short)(slot[j] & 0xffff);
+        const int pos = bucket[j] < 0 ? -1 : hist[bucket[j]] + (slot[j] >> 16);
+        if (pos >= 0) skey[pos] = (unsigned short)(slot[j] & 0xffff);
+        slot[j] = pos;
     }
     for (int a = 0; a < A; ++a) {
         const T* __restrict__ col = static_cast<const T*>(args.a[a]);
-        T v[PER];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int64_t p = base + j * blockDim.x + threadIdx.x;
-            v[j] = pos[j] >= 0 ? __ldcs(col + p) : T(0);
+        for (int j0 = 0; j0 < PER; j0 += 8) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t p = base + (j0 + u) * blockDim.x + threadIdx.x;
+                v[u] = slot[j0 + u] >= 0 ? __ldcs(col + p) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (slot[j0 + u] >= 0) sattr[a * TP + slot[j0 + u]] = v[u];
         }
-#pragma unroll
-        for (int j = 0; j < PER; ++j)
-            if (pos[j] >= 0) sattr[a * TP + pos[j]] = v[j];
     }
     __syncthreads();
     // records out, coalesced
@@ -325,15 +335,15 @@ bool sort_plan(const BinArgs& a, int smem_optin_total, SortDesc* sd) {
         return false;
     const int64_t nb = (B + (1 << log2bk) - 1) >> log2bk;
     if (nb > 8192) return false;
-    // tile: 8 particles per thread of a 512-thread block, halved until the
-    // staged records and the bucket histogram fit
-    int tp = 4096;
-    while (tp > 512 && align256((size_t)(nb + 1) * 4) + align256((size_t)tp * 2) +
-                               (size_t)a.n_attrs * tp * tsz > (size_t)smem_optin)
-        tp >>= 1;
-    if (align256((size_t)(nb + 1) * 4) + align256((size_t)tp * 2) + (size_t)a.n_attrs * tp * tsz >
-        (size_t)smem_optin)
-        return false;
+    // tile: as large as shared memory allows (up to 16384 particles, 32 per
+    // thread of a 512-thread block), so the per-tile bucket table stays
+    // small next to the records; at least 4096 when it fits
+    auto scatter_bytes = [&](int tp_) {
+        return align256((size_t)(nb + 1) * 4) + align256((size_t)tp_ * 2) + (size_t)a.n_attrs * tp_ * tsz;
+    };
+    int tp = 16384;
+    while (tp > 512 && scatter_bytes(tp) > (size_t)smem_optin) tp >>= 1;
+    if (scatter_bytes(tp) > (size_t)smem_optin) return false;
     memset(sd, 0, sizeof *sd);
     sd->log2bk = log2bk;
     sd->nb = (int)nb;
@@ -344,6 +354,7 @@ bool sort_plan(const BinArgs& a, int smem_optin_total, SortDesc* sd) {
     sd->off_skey = (int)align256((size_t)(nb + 1) * 4);
     sd->off_sattr = sd->off_skey + (int)align256((size_t)tp * 2);
     sd->smem_scatter = (size_t)sd->off_sattr + (size_t)a.n_attrs * tp * tsz;
+    sd->per = tp >= 16384 ? 32 : tp >= 8192 ? 16 : 8;
     sd->off_mesh = (int)seg_bytes;
     sd->smem_reduce = seg_bytes + mesh_bytes(a.dtype, mode, 1 << log2bk, a.n_attrs, a.st.do_sum,
                                              a.st.do_min, a.st.do_max);
@@ -365,10 +376,12 @@ size_t sort_scratch_bytes(const SortDesc& sd, const BinArgs& a) {
 
 template <typename T, int A_CT, int MODE>
 static cudaError_t launch_sort_t(const KernelCtx& kc, const BinArgs& a, const SortDesc& sd) {
-    auto scat = k_sort_scatter<T, A_CT>;
+    auto scat = sd.per == 32 ? k_sort_scatter<T, A_CT, 32>
+              : sd.per == 16 ? k_sort_scatter<T, A_CT, 16> : k_sort_scatter<T, A_CT, 8>;
     auto red = k_sort_reduce<T, A_CT, MODE>;
-    static bool configured = false;
-    if (!configured) {
+    static bool configured[3] = {false, false, false};
+    const int ci = sd.per == 32 ? 2 : sd.per == 16 ? 1 : 0;
+    if (!configured[ci]) {
         // the opt-in limit covers static plus dynamic shared memory
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, scat);
@@ -380,9 +393,9 @@ static cudaError_t launch_sort_t(const KernelCtx& kc, const BinArgs& a, const So
             e = cudaFuncSetAttribute(red, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kc.smem_optin - (int)fa.sharedSizeBytes);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured[ci] = true;
     }
-    scat<<<(unsigned)sd.tiles, sd.tp / 8, sd.smem_scatter, kc.stream>>>(a, sd);
+    scat<<<(unsigned)sd.tiles, sd.tp / sd.per, sd.smem_scatter, kc.stream>>>(a, sd);
     {
         dim3 tb(32, 8);
         dim3 tg((unsigned)((sd.tiles + 31) / 32), (unsigned)((sd.nb + 1 + 31) / 32));

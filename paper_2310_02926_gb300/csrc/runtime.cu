@@ -523,9 +523,15 @@ int bn::choose_strategy(const BinArgs& a, int smem_optin, int num_sms, uint32_t 
     // Bucketed sort + reduce when the per-tile bucket table stays small next
     // to the records (few buckets per tile) and there is enough work to
     // stream; otherwise atomics straight into the global mesh.
+    // Bucketed sort + reduce when the mesh state is larger than L2 (so
+    // global atomics would go to DRAM), the per-tile bucket table stays
+    // small next to the records, and there is enough work to stream.
+    const size_t tsz = a.dtype == BN_F64 ? 8 : 4;
+    const double state = (double)B * (8 + a.n_attrs * (8 + 2 * tsz));
+    const double rec = 2.0 + a.n_attrs * (double)tsz;
     SortDesc sd;
-    if (sort_plan(a, smem_optin, &sd) && sd.nb * 4 <= sd.tp && a.n >= (int64_t)num_sms * sd.tp &&
-        a.n >= B / 2)
+    if (state > 128e6 && sort_plan(a, smem_optin, &sd) && (sd.nb + 1) * 4.0 <= 0.5 * rec * sd.tp &&
+        a.n >= (int64_t)num_sms * sd.tp && a.n >= B / 4)
         return BN_STRATEGY_SORT;
     return BN_STRATEGY_GLOBAL;
 }
