@@ -272,13 +272,16 @@ static float trial(bn_context* c, FastBlock f, int strategy, int aggregate, int 
         unsigned char* d = static_cast<unsigned char*>(dev);
         const KernelCtx kc{c->stream, c->num_sms, c->smem_optin, nullptr};
         cudaError_t e = cudaMemcpyAsync(dev, host, L.bytes, cudaMemcpyHostToDevice, c->stream);
+        auto run = [&]() {
+            return queue_batch(kc, dtype, sum_mode, n_attrs, reinterpret_cast<BatchBlock*>(d + L.off_blocks),
+                               reinterpret_cast<int64_t*>(d + L.off_bin_start),
+                               reinterpret_cast<int64_t*>(d + L.off_edge_start),
+                               reinterpret_cast<int4*>(d + L.off_items), reinterpret_cast<int*>(d + L.off_counter),
+                               1, ni, bins, edges, smem, want_avg);
+        };
+        if (e == cudaSuccess) e = run();  // untimed: the first launch also loads the module
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-        if (e == cudaSuccess)
-            e = queue_batch(kc, dtype, sum_mode, n_attrs, reinterpret_cast<BatchBlock*>(d + L.off_blocks),
-                            reinterpret_cast<int64_t*>(d + L.off_bin_start),
-                            reinterpret_cast<int64_t*>(d + L.off_edge_start),
-                            reinterpret_cast<int4*>(d + L.off_items), reinterpret_cast<int*>(d + L.off_counter),
-                            1, ni, bins, edges, smem, want_avg);
+        if (e == cudaSuccess) e = run();
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);

@@ -211,8 +211,12 @@ struct SmemMesh {
                     if (do_sum) st.sum[a][b] = sum_value(k);
                     if (do_mm) {
                         const K2 cur = mm[k];
-                        if (do_min) static_cast<T*>(st.mn[a])[b] = KO::value(cur.x);
-                        if (do_max) static_cast<T*>(st.mx[a])[b] = KO::value(cur.y);
+                        if (st.mmk) {
+                            static_cast<K2*>(st.mmk)[(int64_t)a * st.bins + b] = cur;
+                        } else {
+                            if (do_min) static_cast<T*>(st.mn[a])[b] = KO::value(cur.x);
+                            if (do_max) static_cast<T*>(st.mx[a])[b] = KO::value(cur.y);
+                        }
                     }
                 }
                 continue;
@@ -222,7 +226,13 @@ struct SmemMesh {
             for (int a = 0; a < A; ++a) {
                 const int k = a * B + l;
                 if (do_sum) atomicAdd(&st.sum[a][b], sum_value(k));
-                if (do_mm) {
+                if (do_mm && st.mmk) {
+                    const K2 cur = mm[k];
+                    K2* kp = static_cast<K2*>(st.mmk) + (int64_t)a * st.bins + b;
+                    const K2 g = __ldca(kp);
+                    if (do_min && cur.x < g.x) atomicMin(&kp->x, cur.x);
+                    if (do_max && cur.y > g.y) atomicMax(&kp->y, cur.y);
+                } else if (do_mm) {
                     const K2 cur = mm[k];
                     if (do_min) {
                         const T m = KO::value(cur.x);
@@ -266,6 +276,16 @@ __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, c
             const T x = v[a];
             if (st.do_sum) atomicAdd(&st.sum[a][b], (double)x);
             if (is_nan_bits(x)) continue;
+            if (st.mmk) {
+                // one 16-byte (f64) or 8-byte (f32) read for both keys
+                using KO = KeyOf<T>;
+                auto* kp = static_cast<typename KO::K2*>(st.mmk) + (int64_t)a * st.bins + b;
+                const auto key = KO::key(x);
+                const auto cur = __ldca(kp);
+                if (st.do_min && key < cur.x) atomicMin(&kp->x, key);
+                if (st.do_max && key > cur.y) atomicMax(&kp->y, key);
+                continue;
+            }
             if (st.do_min) {
                 T* g = static_cast<T*>(st.mn[a]) + b;
                 if (total_less(x, filter_load(g))) atomic_min_total(g, x);
@@ -311,6 +331,15 @@ __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, c
     atomicAdd(&st.count[b], (unsigned long long)cnt);
     for (int a = 0; a < A; ++a) {
         if (st.do_sum) atomicAdd(&st.sum[a][b], s[a]);
+        if (st.mmk) {
+            using KO = KeyOf<T>;
+            auto* kp = static_cast<typename KO::K2*>(st.mmk) + (int64_t)a * st.bins + b;
+            const auto cur = __ldca(kp);
+            const auto kl = KO::key(lo[a]), kh = KO::key(hi[a]);
+            if (st.do_min && kl < cur.x) atomicMin(&kp->x, kl);
+            if (st.do_max && kh > cur.y) atomicMax(&kp->y, kh);
+            continue;
+        }
         if (st.do_min && !(lo[a] == pos_inf<T>())) {
             T* g = static_cast<T*>(st.mn[a]) + b;
             if (total_less(lo[a], filter_load(g))) atomic_min_total(g, lo[a]);

@@ -59,6 +59,11 @@ struct StateDesc {
     void* mn[kMaxAttr];
     void* mx[kMaxAttr];
     double* avg[kMaxAttr];
+    // Optional min/max state as interleaved totalOrder keys, [n_attrs][bins]
+    // pairs {min key, max key} (long long for f64, int for f32). When set,
+    // the particle pass updates these instead of mn/mx and k_finalize writes
+    // mn/mx from them; when null, mn/mx hold the running min/max directly.
+    void* mmk;
     int64_t bins;
     int32_t n_attrs;
     int32_t do_sum;  // sums needed (SUM or AVG requested)

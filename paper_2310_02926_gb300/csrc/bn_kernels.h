@@ -29,7 +29,7 @@ cudaError_t launch_bounds_reduce(const KernelCtx& kc, int dtype, const void* x, 
 cudaError_t launch_grid_setup(const KernelCtx& kc, int dtype, const GridDesc& host_desc,
                               const void* bounds_acc, GridDesc* dev_desc, long long* edges0,
                               long long* edges1, double* bounds_out, int* status);
-cudaError_t launch_finalize(const KernelCtx& kc, const StateDesc& st);
+cudaError_t launch_finalize(const KernelCtx& kc, const StateDesc& st, int dtype);
 cudaError_t launch_merge(const KernelCtx& kc, int dtype, const StateDesc& out,
                          const StateDesc* dev_parts, int n_parts);
 cudaError_t launch_gather(const KernelCtx& kc, int dtype, void* dst, const void* src, int64_t n,

@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/binning.h"
@@ -27,6 +29,9 @@ struct bn_context {
     int* status_dev = nullptr;
     int last_strategy = 0;
     bool profile = false;
+    // measured strategy choices of single calls, per shape class
+    std::mutex tune_mu;
+    std::map<std::tuple<int, int, uint32_t, int, int, int>, std::pair<int, int>> tuned;
     std::mutex prof_mu;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pairs;
 

@@ -7,6 +7,7 @@
 
 #include <type_traits>
 
+#include "bn_device.cuh"
 #include "bn_internal.cuh"
 #include "bn_kernels.h"
 
@@ -29,6 +30,15 @@ __global__ void k_init_state(StateDesc st, T* bounds_acc) {
     for (int a = 0; a < st.n_attrs; ++a) {
         if (st.do_sum)
             for (int64_t b = t0; b < B; b += stride) st.sum[a][b] = 0.0;
+        if (st.mmk) {
+            using KO = KeyOf<T>;
+            typename KO::K2 init;
+            init.x = KO::kPosInf;
+            init.y = KO::kNegInf;
+            auto* kp = static_cast<typename KO::K2*>(st.mmk) + (int64_t)a * B;
+            for (int64_t b = t0; b < B; b += stride) kp[b] = init;
+            continue;
+        }
         if (st.do_min) {
             T* p = static_cast<T*>(st.mn[a]);
             for (int64_t b = t0; b < B; b += stride) p[b] = pos_inf<T>();
@@ -186,15 +196,24 @@ __global__ void k_grid_setup(GridDesc host_desc, const T* bounds_acc, GridDesc* 
 // ------------------------------------------------------------------ finalise
 // avg = sum / count in FP64 (round-to-nearest division); empty bins get the
 // quiet NaN 0x7ff8000000000000.
+// With key state (st.mmk), also writes min and max from their keys.
+template <typename T>
 __global__ void k_finalize(StateDesc st) {
     const int64_t B = st.bins;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    using KO = KeyOf<T>;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += stride) {
-        unsigned long long c = st.count[b];
+        unsigned long long c = st.do_avg ? st.count[b] : 0ull;
         double dc = (double)c;
-        for (int a = 0; a < st.n_attrs; ++a)
-            st.avg[a][b] = c ? __ddiv_rn(st.sum[a][b], dc) : qnan;
+        for (int a = 0; a < st.n_attrs; ++a) {
+            if (st.do_avg) st.avg[a][b] = c ? __ddiv_rn(st.sum[a][b], dc) : qnan;
+            if (st.mmk) {
+                const auto k = static_cast<const typename KO::K2*>(st.mmk)[(int64_t)a * B + b];
+                if (st.do_min) static_cast<T*>(st.mn[a])[b] = KO::value(k.x);
+                if (st.do_max) static_cast<T*>(st.mx[a])[b] = KO::value(k.y);
+            }
+        }
     }
 }
 
@@ -300,10 +319,11 @@ cudaError_t launch_grid_setup(const KernelCtx& kc, int dtype, const GridDesc& ho
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const KernelCtx& kc, const StateDesc& st) {
+cudaError_t launch_finalize(const KernelCtx& kc, const StateDesc& st, int dtype) {
     const int block = 256;
     int grid = grid_for(st.bins, block, kc.num_sms * 8);
-    k_finalize<<<grid, block, 0, kc.stream>>>(st);
+    if (dtype == BN_F32) k_finalize<float><<<grid, block, 0, kc.stream>>>(st);
+    else k_finalize<double><<<grid, block, 0, kc.stream>>>(st);
     kc.count_launch();
     return cudaGetLastError();
 }

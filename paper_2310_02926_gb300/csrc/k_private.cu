@@ -65,49 +65,46 @@ __global__ void __launch_bounds__(512) k_bin_private(BinArgs args, int64_t head,
 #pragma unroll
         for (int a = 0; a < AC; ++a)
             AV[a] = reinterpret_cast<const V*>(static_cast<const T*>(args.a[a < A ? a : 0]) + head);
+        // software pipeline: the loads of the next two groups are in flight
+        // while the current two are binned
+        struct Stage {
+            V x[2], y[2], a[2][AC];
+        };
+        auto load = [&](Stage& st, int64_t g) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t gg = g + u * nthreads;
+                if (gg < groups) {
+                    st.x[u] = __ldcs(XV + gg);
+                    st.y[u] = __ldcs(YV + gg);
+#pragma unroll
+                    for (int a = 0; a < A_CT; ++a) st.a[u][a] = __ldcs(AV[a] + gg);
+                }
+            }
+        };
+        auto consume = [&](const Stage& st, int64_t g) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (g + u * nthreads >= groups) break;
+#pragma unroll
+                for (int j = 0; j < VN; ++j) {
+                    const int b = binner.bin(vget<T>(st.x[u], j), vget<T>(st.y[u], j));
+                    if (b >= 0) {
+                        m.add_count(b);
+#pragma unroll
+                        for (int a = 0; a < A_CT; ++a) m.add(a, b, vget<T>(st.a[u][a], j));
+                    }
+                }
+            }
+        };
+        Stage cur, nxt;
         int64_t gi = tid;
-        for (; gi + nthreads < groups; gi += 2 * nthreads) {
-            V x0 = __ldcs(XV + gi), y0 = __ldcs(YV + gi);
-            V x1 = __ldcs(XV + gi + nthreads), y1 = __ldcs(YV + gi + nthreads);
-            V a0[AC], a1[AC];
-#pragma unroll
-            for (int a = 0; a < A_CT; ++a) {
-                a0[a] = __ldcs(AV[a] + gi);
-                a1[a] = __ldcs(AV[a] + gi + nthreads);
-            }
-#pragma unroll
-            for (int j = 0; j < VN; ++j) {
-                int b = binner.bin(vget<T>(x0, j), vget<T>(y0, j));
-                if (b >= 0) {
-                    m.add_count(b);
-#pragma unroll
-                    for (int a = 0; a < A_CT; ++a) m.add(a, b, vget<T>(a0[a], j));
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < VN; ++j) {
-                int b = binner.bin(vget<T>(x1, j), vget<T>(y1, j));
-                if (b >= 0) {
-                    m.add_count(b);
-#pragma unroll
-                    for (int a = 0; a < A_CT; ++a) m.add(a, b, vget<T>(a1[a], j));
-                }
-            }
-        }
-        for (; gi < groups; gi += nthreads) {
-            V x0 = __ldcs(XV + gi), y0 = __ldcs(YV + gi);
-            V a0[AC];
-#pragma unroll
-            for (int a = 0; a < A_CT; ++a) a0[a] = __ldcs(AV[a] + gi);
-#pragma unroll
-            for (int j = 0; j < VN; ++j) {
-                int b = binner.bin(vget<T>(x0, j), vget<T>(y0, j));
-                if (b >= 0) {
-                    m.add_count(b);
-#pragma unroll
-                    for (int a = 0; a < A_CT; ++a) m.add(a, b, vget<T>(a0[a], j));
-                }
-            }
+        if (gi < groups) load(cur, gi);
+        for (; gi < groups; gi += 2 * nthreads) {
+            const int64_t gn = gi + 2 * nthreads;
+            if (gn < groups) load(nxt, gn);
+            consume(cur, gi);
+            cur = nxt;
         }
     } else {
         for (int64_t gi = tid; gi < groups; gi += nthreads) {

@@ -341,7 +341,11 @@ bool sort_plan(const BinArgs& a, int smem_optin_total, SortDesc* sd) {
     auto scatter_bytes = [&](int tp_) {
         return align256((size_t)(nb + 1) * 4) + align256((size_t)tp_ * 2) + (size_t)a.n_attrs * tp_ * tsz;
     };
-    int tp = 16384;
+    // smallest tile from 4096 up whose bucket table stays under a quarter of
+    // the tile's record bytes, then shrunk to what shared memory holds
+    const double rec = 2.0 + (double)a.n_attrs * tsz;
+    int tp = 4096;
+    while (tp < 16384 && (double)(nb + 1) * 4.0 > 0.25 * rec * tp) tp <<= 1;
     while (tp > 512 && scatter_bytes(tp) > (size_t)smem_optin) tp >>= 1;
     if (scatter_bytes(tp) > (size_t)smem_optin) return false;
     memset(sd, 0, sizeof *sd);

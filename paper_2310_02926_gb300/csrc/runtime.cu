@@ -634,6 +634,48 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
 
     const KernelCtx kc = plan.kc();
     cudaError_t e;
+    args.grid = gd;
+    // strategy first: the global strategy keeps min/max as key pairs in a
+    // temporary (one read per attribute in the hot loop), written to the
+    // outputs by the finalise kernel
+    int strat = 0;
+    SortDesc sortd;
+    void* sort_scratch = nullptr;
+    bool trial = false;  // measure the candidates on this call's data first
+    std::tuple<int, int, uint32_t, int, int, int> klass;
+    const uint32_t forced = ops & BN_STRATEGY_MASK;
+    const uint32_t aggbits = ops & BN_AGG_MASK;
+    if (n > 0) {
+        strat = choose_strategy(args, c->smem_optin, c->num_sms, ops);
+        if (!forced) {
+            // shape class: dtype, attributes, ops, log2 bins, log2 n, auto bounds
+            auto lg = [](int64_t v) { int r = 0; while (v > 1) v >>= 1, ++r; return r; };
+            klass = std::make_tuple(dtype, n_attrs, ops & (BN_OP_ALL | BN_SUM_MASK), lg(B), lg(n),
+                                    grid->auto_bounds ? 1 : 0);
+            std::lock_guard<std::mutex> lk(c->tune_mu);
+            auto it = c->tuned.find(klass);
+            if (it != c->tuned.end()) {
+                strat = it->second.first;
+                if (!aggbits) args.aggregate = it->second.second;
+            } else if (n >= (int64_t)1 << 20 && !accumulate) {
+                trial = true;
+            }
+        }
+        if (strat == BN_STRATEGY_PRIVATE && private_smem_bytes(args, c->smem_optin) == 0)
+            return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_PRIVATE: the mesh does not fit in shared memory");
+        const bool sort_ok = sort_plan(args, c->smem_optin, &sortd);
+        if (strat == BN_STRATEGY_SORT && !sort_ok)
+            return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_SORT: the mesh has too many buckets for the sort path");
+        if (strat == BN_STRATEGY_SORT || (trial && sort_ok)) {
+            sort_scratch = plan.alloc(sort_scratch_bytes(sortd, args));
+            if (!sort_scratch) return cuda_fail(plan.err, "cudaMallocAsync(sort scratch)");
+        }
+        if ((strat == BN_STRATEGY_GLOBAL || trial) && !accumulate && n_attrs > 0 && (want_min || want_max)) {
+            sd.mmk = plan.alloc((size_t)n_attrs * B * 2 * dtype_size(dtype));
+            if (!sd.mmk) return cuda_fail(plan.err, "cudaMallocAsync(min/max keys)");
+        }
+    }
+    args.st = sd;
     void* bounds_acc = nullptr;
     if (grid->auto_bounds) {
         bounds_acc = plan.alloc(4 * dtype_size(dtype));
@@ -664,24 +706,67 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         args.dev_grid = dev_grid;
     }
     args.grid = gd;
-    if (n > 0) {
-        int strat = choose_strategy(args, c->smem_optin, c->num_sms, ops);
-        if (strat == BN_STRATEGY_PRIVATE && private_smem_bytes(args, c->smem_optin) == 0)
-            return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_PRIVATE: the mesh does not fit in shared memory");
-        SortDesc sd;
-        void* sort_scratch = nullptr;
-        if (strat == BN_STRATEGY_SORT) {
-            if (!sort_plan(args, c->smem_optin, &sd))
-                return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_SORT: the mesh has too many buckets for the sort path");
-            sort_scratch = plan.alloc(sort_scratch_bytes(sd, args));
-            if (!sort_scratch) return cuda_fail(plan.err, "cudaMallocAsync(sort scratch)");
+    if (n > 0 && trial) {
+        // Autotuner: run each candidate particle pass on this call's data,
+        // timed with CUDA events (the state is re-initialised before each),
+        // keep the fastest for the shape class, then do the real pass.
+        struct Cand { int strat, agg; };
+        std::vector<Cand> cands;
+        if (private_smem_bytes(args, c->smem_optin) > 0) cands.push_back({BN_STRATEGY_PRIVATE, 0});
+        cands.push_back({BN_STRATEGY_GLOBAL, 0});
+        cands.push_back({BN_STRATEGY_GLOBAL, 1});
+        if (sort_scratch) cands.push_back({BN_STRATEGY_SORT, 0});
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        float best = -1.0f;
+        Cand win{strat, args.aggregate};
+        if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+            for (const Cand& cd : cands) {
+                BinArgs ta = args;
+                ta.aggregate = aggbits == BN_AGG_ON ? 1 : aggbits == BN_AGG_OFF ? 0 : cd.agg;
+                if (cd.strat != BN_STRATEGY_GLOBAL) ta.st.mmk = nullptr;
+                auto pass = [&]() {
+                    return cd.strat == BN_STRATEGY_PRIVATE ? launch_bin_private(kc, ta)
+                           : cd.strat == BN_STRATEGY_SORT  ? launch_bin_sort(kc, ta, sortd, sort_scratch)
+                                                           : launch_bin_global(kc, ta);
+                };
+                // one untimed pass first: the first launch of a kernel also
+                // loads its module, which must not count against it
+                e = launch_init_state(kc, dtype, ta.st, nullptr);
+                if (e == cudaSuccess) e = pass();
+                if (e == cudaSuccess) e = launch_init_state(kc, dtype, ta.st, nullptr);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, plan.stream);
+                if (e == cudaSuccess) e = pass();
+                if (e == cudaSuccess) e = cudaEventRecord(e1, plan.stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = -1.0f;
+                if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) break;
+                if (ms >= 0.0f && (best < 0.0f || ms < best)) {
+                    best = ms;
+                    win = cd;
+                }
+            }
         }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e != cudaSuccess) return cuda_fail(e, "autotuner trial");
+        strat = win.strat;
+        if (!aggbits) args.aggregate = win.agg;
+        {
+            std::lock_guard<std::mutex> lk(c->tune_mu);
+            c->tuned[klass] = std::make_pair(win.strat, win.agg);
+        }
+        if (strat != BN_STRATEGY_GLOBAL) sd.mmk = nullptr;
+        e = launch_init_state(kc, dtype, sd, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    }
+    if (n > 0) {
         plan.strategy = strat;
         cudaEvent_t t0 = nullptr, t1 = nullptr;
         if (c->profile && cudaEventCreate(&t0) == cudaSuccess && cudaEventCreate(&t1) == cudaSuccess)
             cudaEventRecord(t0, plan.stream);
         e = strat == BN_STRATEGY_PRIVATE ? launch_bin_private(kc, args)
-            : strat == BN_STRATEGY_SORT  ? launch_bin_sort(kc, args, sd, sort_scratch)
+            : strat == BN_STRATEGY_SORT  ? launch_bin_sort(kc, args, sortd, sort_scratch)
                                          : launch_bin_global(kc, args);
         if (t1) {
             cudaEventRecord(t1, plan.stream);
@@ -690,8 +775,8 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         }
         if (e != cudaSuccess) return cuda_fail(e, "binning kernel");
     }
-    if (want_avg) {
-        e = launch_finalize(kc, sd);
+    if (want_avg || sd.mmk) {
+        e = launch_finalize(kc, sd, dtype);
         if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
     }
     return BN_OK;
@@ -818,7 +903,7 @@ extern "C" bn_status bn_merge_results(bn_context* c, const bn_result* parts, int
         cudaError_t e = cudaMemcpyAsync(dparts, hp.data(), sizeof(StateDesc) * n_parts,
                                         cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = launch_merge(c->kc(), dtype, sd, dparts, n_parts);
-        if (e == cudaSuccess && want_avg) e = launch_finalize(c->kc(), sd);
+        if (e == cudaSuccess && want_avg) e = launch_finalize(c->kc(), sd, dtype);
         if (e != cudaSuccess) st = cuda_fail(e, "merge kernels");
     }
     if (st == BN_OK) st = plan.finish(r);

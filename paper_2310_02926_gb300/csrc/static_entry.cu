@@ -193,7 +193,7 @@ extern "C" bn_status bn_bin_particles_static(const bn_buffer* x, const bn_buffer
         int strat = choose_strategy(args, optin, sms, ops);
         e = strat == BN_STRATEGY_PRIVATE ? launch_bin_private(kc, args) : launch_bin_global(kc, args);
     }
-    if (e == cudaSuccess && want_avg) e = launch_finalize(kc, sd);
+    if (e == cudaSuccess && want_avg) e = launch_finalize(kc, sd, dtype);
     if (e != cudaSuccess) return cuda_fail(e, "bn_bin_particles_static: launch");
     if (!sync) return BN_OK;
     e = cudaStreamSynchronize(s);
