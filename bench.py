@@ -66,7 +66,7 @@ WORKLOADS = {
 }
 # kernel sources whose ncu traffic record applies, per particle-pass strategy
 KERNEL_SOURCES = {
-    "global": ["paper_2310_02926_gb300/csrc/k_global.cu"],
+    "global": ["paper_2310_02926_gb300/csrc/k_global.cu", "paper_2310_02926_gb300/csrc/bn_device.cuh"],
     "private": ["paper_2310_02926_gb300/csrc/k_private.cu", "paper_2310_02926_gb300/csrc/bn_device.cuh"],
     "sort": ["paper_2310_02926_gb300/csrc/k_sort.cu", "paper_2310_02926_gb300/csrc/bn_device.cuh"],
 }
