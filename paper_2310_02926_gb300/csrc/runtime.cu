@@ -657,7 +657,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
             if (it != c->tuned.end()) {
                 strat = it->second.first;
                 if (!aggbits) args.aggregate = it->second.second;
-            } else if (n >= (int64_t)1 << 20 && !accumulate) {
+            } else if (n >= (int64_t)1 << 16 && !accumulate) {
                 trial = true;
             }
         }
