@@ -575,6 +575,7 @@ def main():
         elapsed_ms = ev0.elapsed_time(ev1)
         gpu_launches = ctx.launches - launches0
         kern_ms, kern_launches, strategy = bn.bn_context_profile(ctx.handle)
+        tuning = bn.bn_context_autotune_report(ctx.handle).strip().splitlines()
         time.sleep(0.3)
         clocks.stop()
         clk = clocks.summary(t_wall0, t_wall1)
@@ -630,6 +631,7 @@ def main():
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dt_label, "data": "synthetic",
             "config": dict(workload_config(args.workload, N_PART, bytes_in), strategy=strategy,
+                           autotuner=tuning,
                            sum_mode=args.sum if dt_label == "f32" else "f64",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
             "hbm_frac_step": step_gbs / hbm,

@@ -249,6 +249,11 @@ BN_API bn_status bn_context_destroy(bn_context* ctx);
 /* The cudaStream_t the context executes on (for timing with events). */
 BN_API bn_status bn_context_stream(bn_context* ctx, void** stream);
 
+/* The autotuner's record: one line per tuned shape class with the measured
+ * time of each candidate particle pass and the choice, written into buf
+ * (NUL-terminated, truncated to cap bytes). */
+BN_API bn_status bn_context_autotune_report(bn_context* ctx, char* buf, size_t cap);
+
 /* Number of kernel launches the context has issued so far. */
 BN_API bn_status bn_context_launch_count(bn_context* ctx, uint64_t* launches);
 

@@ -176,6 +176,12 @@ def bn_context_profile(ctx: int):
     return ms.value, n.value, STRATEGY_NAMES.get(st.value, "none")
 
 
+def bn_context_autotune_report(ctx: int) -> str:
+    buf = ctypes.create_string_buffer(16384)
+    check(lib().bn_context_autotune_report(ctx, buf, len(buf)))
+    return buf.value.decode()
+
+
 def bn_context_launch_count(ctx: int) -> int:
     n = ctypes.c_uint64()
     check(lib().bn_context_launch_count(ctx, ctypes.byref(n)))

@@ -111,6 +111,7 @@ PROTOTYPES = {
     "bn_context_destroy": (S, [P]),
     "bn_context_stream": (S, [P, PP]),
     "bn_context_launch_count": (S, [P, ctypes.POINTER(ctypes.c_uint64)]),
+    "bn_context_autotune_report": (S, [P, ctypes.c_char_p, ctypes.c_size_t]),
     "bn_context_profile": (S, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
                               ctypes.POINTER(ctypes.c_int32)]),
     "bn_bin_particles": (S, [P, ctypes.POINTER(bn_buffer), ctypes.POINTER(bn_buffer),

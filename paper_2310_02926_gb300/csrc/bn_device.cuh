@@ -260,9 +260,23 @@ __device__ __forceinline__ T filter_load(const T* p) { return __ldca(p); }
 // Combine the lanes of the calling warp that share bin b (b >= 0) and let
 // the lowest such lane update the global mesh. Every lane of the warp must
 // call it (b = -1 for lanes without an in-bounds particle).
+// Shared-memory window of the global strategy: count and sums of the bins
+// [x0, x0 + nx) x [y0, y0 + ny) of a res_x-wide mesh, for one CTA.
+struct SmemWindow {
+    unsigned int* cnt;  // [nx * ny]
+    double* sum;        // [A][nx * ny]
+    int x0, y0, nx, ny, rx, W;
+    __device__ __forceinline__ int slot(int b) const {
+        if (nx == 0) return -1;
+        const int iy = b / rx, ix = b - iy * rx;
+        const int wx = ix - x0, wy = iy - y0;
+        return ((unsigned)wx < (unsigned)nx && (unsigned)wy < (unsigned)ny) ? wy * nx + wx : -1;
+    }
+};
+
 template <typename T, int A_CT>
 __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, const T* v,
-                                            bool aggregate) {
+                                            bool aggregate, const SmemWindow* win = nullptr) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned peers = aggregate ? __match_any_sync(full, b) : (1u << lane);
@@ -271,10 +285,15 @@ __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, c
     if (!aggregate || __all_sync(full, alone || b < 0)) {
         // no two lanes share a bin: skip the combining shuffles
         if (b < 0) return;
-        atomicAdd(&st.count[b], 1ull);
+        const int ws = win ? win->slot(b) : -1;
+        if (ws >= 0) atomicAdd(&win->cnt[ws], 1u);
+        else atomicAdd(&st.count[b], 1ull);
         for (int a = 0; a < A; ++a) {
             const T x = v[a];
-            if (st.do_sum) atomicAdd(&st.sum[a][b], (double)x);
+            if (st.do_sum) {
+                if (ws >= 0) atomicAdd(&win->sum[a * win->W + ws], (double)x);
+                else atomicAdd(&st.sum[a][b], (double)x);
+            }
             if (is_nan_bits(x)) continue;
             if (st.mmk) {
                 // one 16-byte (f64) or 8-byte (f32) read for both keys
@@ -328,9 +347,14 @@ __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, c
         }
     }
     if (b < 0 || lane != leader) return;
-    atomicAdd(&st.count[b], (unsigned long long)cnt);
+    const int ws = win ? win->slot(b) : -1;
+    if (ws >= 0) atomicAdd(&win->cnt[ws], cnt);
+    else atomicAdd(&st.count[b], (unsigned long long)cnt);
     for (int a = 0; a < A; ++a) {
-        if (st.do_sum) atomicAdd(&st.sum[a][b], s[a]);
+        if (st.do_sum) {
+            if (ws >= 0) atomicAdd(&win->sum[a * win->W + ws], s[a]);
+            else atomicAdd(&st.sum[a][b], s[a]);
+        }
         if (st.mmk) {
             using KO = KeyOf<T>;
             auto* kp = static_cast<typename KO::K2*>(st.mmk) + (int64_t)a * st.bins + b;

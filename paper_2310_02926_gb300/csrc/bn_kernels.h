@@ -42,6 +42,10 @@ struct BinArgs {
     int n_attrs;
     int sum_mode;           // SumMode (f32 data)
     int aggregate;          // global strategy: combine same-bin lanes of a warp first
+    // global strategy: a window of bins whose count and sums each CTA keeps
+    // in shared memory (win_nx == 0: none); bins [win_x0, win_x0 + win_nx) x
+    // [win_y0, win_y0 + win_ny)
+    int win_x0, win_y0, win_nx, win_ny;
     const void* x;
     const void* y;
     const void* a[kMaxAttr];
@@ -105,5 +109,6 @@ size_t private_mesh_bytes(int dtype, int sum_mode, int64_t bins, int n_attrs, bo
 size_t private_smem_bytes(const BinArgs& a, int smem_optin);
 cudaError_t launch_bin_private(const KernelCtx& kc, const BinArgs& a);
 cudaError_t launch_bin_global(const KernelCtx& kc, const BinArgs& a);
+size_t global_window_bytes(int win_cells, int n_attrs, bool do_sum);
 
 }  // namespace bn

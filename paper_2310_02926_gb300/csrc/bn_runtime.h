@@ -6,6 +6,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -31,7 +32,12 @@ struct bn_context {
     bool profile = false;
     // measured strategy choices of single calls, per shape class
     std::mutex tune_mu;
-    std::map<std::tuple<int, int, uint32_t, int, int, int>, std::pair<int, int>> tuned;
+    struct Tuned {
+        int strategy, aggregate;
+        int win_x0, win_y0, win_nx, win_ny;  // global strategy's shared-memory window
+    };
+    std::map<std::tuple<int, int, uint32_t, int, int, int>, Tuned> tuned;
+    std::vector<std::string> tune_log;  // one line per tuned class
     std::mutex prof_mu;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pairs;
 

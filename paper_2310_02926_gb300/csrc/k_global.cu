@@ -62,6 +62,7 @@ template <> struct GBinner<double> {
 
 template <typename T, int A_CT>
 __global__ void __launch_bounds__(256) k_bin_global(BinArgs args, int64_t head, int64_t groups) {
+    extern __shared__ __align__(16) unsigned char wsmem[];
     using V = typename GVec<T>::type;
     constexpr int VN = GVec<T>::N;
     constexpr int AC = A_CT > 0 ? A_CT : kMaxAttr;
@@ -78,6 +79,25 @@ __global__ void __launch_bounds__(256) k_bin_global(BinArgs args, int64_t head, 
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 
+    // optional shared-memory window (count and sums of the densest bins)
+    SmemWindow wv;
+    const SmemWindow* win = nullptr;
+    if (args.win_nx > 0) {
+        wv.x0 = args.win_x0;
+        wv.y0 = args.win_y0;
+        wv.nx = args.win_nx;
+        wv.ny = args.win_ny;
+        wv.rx = g.ax[0].res;
+        wv.W = args.win_nx * args.win_ny;
+        wv.cnt = reinterpret_cast<unsigned int*>(wsmem);
+        wv.sum = reinterpret_cast<double*>(wsmem + (((size_t)wv.W * 4 + 15) & ~(size_t)15));
+        for (int k = threadIdx.x; k < wv.W; k += blockDim.x) wv.cnt[k] = 0u;
+        if (st.do_sum)
+            for (int k = threadIdx.x; k < A * wv.W; k += blockDim.x) wv.sum[k] = 0.0;
+        __syncthreads();
+        win = &wv;
+    }
+
     // scalar head and tail: whole warps iterate together (warp_commit needs
     // every lane), lanes past the end pass b = -1
     const int64_t tail0 = head + groups * VN;
@@ -91,7 +111,7 @@ __global__ void __launch_bounds__(256) k_bin_global(BinArgs args, int64_t head, 
                 b = binner.bin(X[i], Y[i]);
                 for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(args.a[a])[i];
             }
-            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0);
+            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0, win);
         }
     };
     scalar_range(0, head);
@@ -127,7 +147,20 @@ __global__ void __launch_bounds__(256) k_bin_global(BinArgs args, int64_t head, 
                     for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(args.a[a])[i];
                 }
             }
-            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0);
+            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0, win);
+        }
+    }
+    if (win) {
+        // this CTA's window partials into the global mesh
+        __syncthreads();
+        for (int k = threadIdx.x; k < wv.W; k += blockDim.x) {
+            const unsigned int c = wv.cnt[k];
+            if (!c) continue;
+            const int wy = k / wv.nx, wx = k - wy * wv.nx;
+            const int64_t b = (int64_t)(wv.y0 + wy) * wv.rx + (wv.x0 + wx);
+            atomicAdd(&st.count[b], (unsigned long long)c);
+            if (st.do_sum)
+                for (int a = 0; a < A; ++a) atomicAdd(&st.sum[a][b], wv.sum[a * wv.W + k]);
         }
     }
 }
@@ -151,6 +184,11 @@ static void gvector_split(const BinArgs& a, int64_t* head, int64_t* groups) {
     *groups = (a.n - h) / VN;
 }
 
+size_t global_window_bytes(int win_cells, int n_attrs, bool do_sum) {
+    if (win_cells <= 0) return 0;
+    return (((size_t)win_cells * 4 + 15) & ~(size_t)15) + (do_sum ? (size_t)n_attrs * win_cells * 8 : 0);
+}
+
 template <typename T, int A_CT>
 static cudaError_t launch_global_t(const KernelCtx& kc, const BinArgs& a) {
     int64_t head, groups;
@@ -159,9 +197,30 @@ static cudaError_t launch_global_t(const KernelCtx& kc, const BinArgs& a) {
     int64_t work = groups > 0 ? groups : a.n;
     int64_t grid = (work + block - 1) / block;
     int64_t cap = (int64_t)kc.num_sms * 8;
+    size_t smem = 0;
+    auto kern = k_bin_global<T, A_CT>;
+    if (a.win_nx > 0) {
+        // one window copy per CTA: as many CTAs as fit, all resident
+        smem = global_window_bytes(a.win_nx * a.win_ny, a.n_attrs, a.st.do_sum != 0);
+        static bool configured = false;
+        if (!configured) {
+            cudaFuncAttributes fa;
+            cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kc.smem_optin - (int)fa.sharedSizeBytes);
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        cap = (int64_t)kc.num_sms * per_sm;
+    }
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    k_bin_global<T, A_CT><<<(int)grid, block, 0, kc.stream>>>(a, head, groups);
+    kern<<<(int)grid, block, smem, kc.stream>>>(a, head, groups);
     kc.count_launch();
     return cudaGetLastError();
 }

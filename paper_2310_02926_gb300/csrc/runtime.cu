@@ -166,6 +166,19 @@ extern "C" bn_status bn_context_profile(bn_context* c, double* total_ms, uint64_
     return st;
 }
 
+extern "C" bn_status bn_context_autotune_report(bn_context* c, char* buf, size_t cap) {
+    if (!c || !buf || cap == 0) return fail(BN_ERR_INVALID_ARG, "bn_context_autotune_report: bad arguments");
+    std::string all;
+    {
+        std::lock_guard<std::mutex> lk(c->tune_mu);
+        for (const std::string& l : c->tune_log) all += l + "\n";
+    }
+    const size_t k = std::min(all.size(), cap - 1);
+    memcpy(buf, all.data(), k);
+    buf[k] = '\0';
+    return BN_OK;
+}
+
 extern "C" bn_status bn_context_launch_count(bn_context* c, uint64_t* n) {
     if (!c || !n) return fail(BN_ERR_INVALID_ARG, "bn_context_launch_count: NULL argument");
     *n = c->launches.load();
@@ -655,8 +668,16 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
             std::lock_guard<std::mutex> lk(c->tune_mu);
             auto it = c->tuned.find(klass);
             if (it != c->tuned.end()) {
-                strat = it->second.first;
-                if (!aggbits) args.aggregate = it->second.second;
+                strat = it->second.strategy;
+                if (!aggbits) args.aggregate = it->second.aggregate;
+                if (strat == BN_STRATEGY_GLOBAL && it->second.win_nx > 0 &&
+                    it->second.win_x0 + it->second.win_nx <= grid->res[0] &&
+                    it->second.win_y0 + it->second.win_ny <= grid->res[1]) {
+                    args.win_x0 = it->second.win_x0;
+                    args.win_y0 = it->second.win_y0;
+                    args.win_nx = it->second.win_nx;
+                    args.win_ny = it->second.win_ny;
+                }
             } else if (n >= (int64_t)1 << 16 && !accumulate) {
                 trial = true;
             }
@@ -719,6 +740,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         float best = -1.0f;
         Cand win{strat, args.aggregate};
+        std::string times;
         if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
             for (const Cand& cd : cands) {
                 BinArgs ta = args;
@@ -741,9 +763,97 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
                 float ms = -1.0f;
                 if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
                 if (e != cudaSuccess) break;
+                char tb[64];
+                snprintf(tb, sizeof tb, " %s%s=%.3fms",
+                         cd.strat == BN_STRATEGY_PRIVATE ? "private" : cd.strat == BN_STRATEGY_SORT ? "sort" : "global",
+                         cd.strat == BN_STRATEGY_GLOBAL ? (ta.aggregate ? "+agg" : "") : "", ms);
+                times += tb;
                 if (ms >= 0.0f && (best < 0.0f || ms < best)) {
                     best = ms;
                     win = cd;
+                }
+            }
+        }
+        // Global strategy with a shared-memory window over the densest bins:
+        // the window is placed on the counts the trials just produced (in situ
+        // steps keep their distribution from one step to the next) and kept
+        // only if it is faster.
+        int wbest[4] = {0, 0, 0, 0};
+        if (e == cudaSuccess && win.strat == BN_STRATEGY_GLOBAL && private_smem_bytes(args, c->smem_optin) == 0) {
+            const int rx = grid->res[0], ry = grid->res[1];
+            int cells = 0;
+            while (global_window_bytes(cells + 64, n_attrs, sd.do_sum != 0) <= (size_t)(c->smem_optin - 2048))
+                cells += 64;
+            int side = (int)std::sqrt((double)cells);
+            const int wnx = std::min(side, rx), wny = std::min(cells / std::max(wnx, 1), ry);
+            if (wnx >= 8 && wny >= 8 && (int64_t)wnx * wny < B) {
+                std::vector<unsigned long long> cnt((size_t)B);
+                e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(cnt.data(), sd.count, (size_t)B * 8, cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess) {
+                    // 2D prefix sums, then every window position
+                    std::vector<unsigned long long> P((size_t)(rx + 1) * (ry + 1), 0ull);
+                    for (int yy = 0; yy < ry; ++yy)
+                        for (int xx = 0; xx < rx; ++xx)
+                            P[(size_t)(yy + 1) * (rx + 1) + xx + 1] = cnt[(size_t)yy * rx + xx] +
+                                P[(size_t)yy * (rx + 1) + xx + 1] + P[(size_t)(yy + 1) * (rx + 1) + xx] -
+                                P[(size_t)yy * (rx + 1) + xx];
+                    unsigned long long bestc = 0;
+                    for (int yy = 0; yy + wny <= ry; ++yy)
+                        for (int xx = 0; xx + wnx <= rx; ++xx) {
+                            const unsigned long long cw =
+                                P[(size_t)(yy + wny) * (rx + 1) + xx + wnx] - P[(size_t)yy * (rx + 1) + xx + wnx] -
+                                P[(size_t)(yy + wny) * (rx + 1) + xx] + P[(size_t)yy * (rx + 1) + xx];
+                            if (cw > bestc) {
+                                bestc = cw;
+                                wbest[0] = xx;
+                                wbest[1] = yy;
+                            }
+                        }
+                    // worth trying only if the window holds a good share of the particles
+                    if (bestc * 8 >= (unsigned long long)n) {
+                        wbest[2] = wnx;
+                        wbest[3] = wny;
+                        BinArgs ta = args;
+                        ta.aggregate = aggbits == BN_AGG_ON ? 1 : aggbits == BN_AGG_OFF ? 0 : win.agg;
+                        ta.win_x0 = wbest[0];
+                        ta.win_y0 = wbest[1];
+                        ta.win_nx = wnx;
+                        ta.win_ny = wny;
+                        if (e0) cudaEventDestroy(e0);
+                        if (e1) cudaEventDestroy(e1);
+                        e0 = e1 = nullptr;
+                        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+                        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+                        float ms = -1.0f;
+                        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                            e = launch_init_state(kc, dtype, ta.st, nullptr);
+                            if (e == cudaSuccess && rep == 1) e = cudaEventRecord(e0, plan.stream);
+                            if (e == cudaSuccess) e = launch_bin_global(kc, ta);
+                            if (e == cudaSuccess && rep == 1) e = cudaEventRecord(e1, plan.stream);
+                        }
+                        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                        {
+                            char tb[96];
+                            snprintf(tb, sizeof tb, " global+window[%d,%d %dx%d holding %.0f%%]=%.3fms", wbest[0],
+                                     wbest[1], wnx, wny, 100.0 * (double)bestc / (double)n, ms);
+                            times += tb;
+                        }
+                        if (e == cudaSuccess && ms >= 0.0f && ms < best) {
+                            best = ms;
+                            args.win_x0 = wbest[0];
+                            args.win_y0 = wbest[1];
+                            args.win_nx = wnx;
+                            args.win_ny = wny;
+                        } else {
+                            wbest[2] = wbest[3] = 0;
+                        }
+                        if (e0) cudaEventDestroy(e0);
+                        if (e1) cudaEventDestroy(e1);
+                        e0 = e1 = nullptr;
+                    }
                 }
             }
         }
@@ -754,7 +864,15 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         if (!aggbits) args.aggregate = win.agg;
         {
             std::lock_guard<std::mutex> lk(c->tune_mu);
-            c->tuned[klass] = std::make_pair(win.strat, win.agg);
+            c->tuned[klass] = bn_context::Tuned{win.strat, win.agg, wbest[0], wbest[1], wbest[2], wbest[3]};
+            char head[160];
+            snprintf(head, sizeof head, "dtype=%s attrs=%d bins=2^%d n=2^%d:", dtype == BN_F64 ? "f64" : "f32",
+                     n_attrs, std::get<3>(klass), std::get<4>(klass));
+            char tail[96];
+            snprintf(tail, sizeof tail, " -> %s%s%s",
+                     win.strat == BN_STRATEGY_PRIVATE ? "private" : win.strat == BN_STRATEGY_SORT ? "sort" : "global",
+                     win.strat == BN_STRATEGY_GLOBAL && win.agg ? "+agg" : "", wbest[2] ? "+window" : "");
+            c->tune_log.push_back(std::string(head) + times + tail);
         }
         if (strat != BN_STRATEGY_GLOBAL) sd.mmk = nullptr;
         e = launch_init_state(kc, dtype, sd, nullptr);

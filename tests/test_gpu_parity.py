@@ -81,6 +81,20 @@ def test_sort_splits_dense_bucket_across_items(bn, ctx, dtype):
     check(w, run_gpu(ctx, w, flags=bn.STRATEGY_SORT), TOL_F64 if dtype == np.float64 else TOL_F32C)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_autotuned_calls_repeat_exactly(bn, dtype):
+    """A fresh context tunes on the first call of a shape (global may get a
+    shared-memory window over the densest bins); later calls reuse the
+    choice. Every call must match the oracle."""
+    c = bn.Context(0)
+    try:
+        for seed in (51, 52, 53):
+            w = workloads.plummer(3_000_000, seed=seed, dtype=dtype, res=1024)
+            check(w, run_gpu(c, w), TOL_F64 if dtype == np.float64 else TOL_F32C, label=f"seed {seed}")
+    finally:
+        c.close()
+
+
 def test_private_rejects_mesh_too_large_for_shared_memory(bn, ctx):
     w = workloads.plummer(10_000, seed=2, dtype=np.float64, res=1024)
     with pytest.raises(bn.BinningError) as e:
