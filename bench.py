@@ -325,7 +325,10 @@ def run_batch(args, n_blocks):
         ms_b, launches_b = timed(batched, args.steps, args.warmup)
         ms_p, launches_p = timed(plain, max(1, args.steps // 4), 1)
     bytes32 = total * 16
+    bins_total = sum(int(plan.sides[k]) ** 2 for k in range(plan.n_blocks))
+    out_bytes = bins_total * (8 + 2 * (8 + 4 + 4 + 8))   # count, and sum/min/max/avg per attribute
     hbm, peak_src = peaks()
+    tuning = bn.bn_context_autotune_report(ctx.handle).strip().splitlines()
     line = {"metric": METRIC, "value": total / (ms_b / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -335,10 +338,13 @@ def run_batch(args, n_blocks):
                        "sum_mode": "f32c", "l2": "inputs 4+ GB > L2"},
             "batched_fp32": {"particles_per_s": total / (ms_b / 1e3), "ms": ms_b,
                              "hbm_frac_read": bytes32 / (ms_b / 1e3) / 1e9 / hbm,
+                             "hbm_frac_algorithmic": (bytes32 + out_bytes) / (ms_b / 1e3) / 1e9 / hbm,
                              "gpu_launches_per_step": launches_b},
             "plain_fp64": {"particles_per_s": total / (ms_p / 1e3), "ms": ms_p,
                            "gpu_launches_per_step": launches_p},
             "speedup_batched_fp32_vs_plain_fp64": ms_p / ms_b,
+            "bins_total": bins_total, "output_bytes": out_bytes,
+            "autotuner": tuning,
             "data_generation_s": gen_s}
     if args.check:
         worst = 0.0

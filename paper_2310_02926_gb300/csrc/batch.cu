@@ -230,7 +230,7 @@ static void fill_plan(std::vector<FastBlock>& fbs, const PlanLayout& L, unsigned
     int ni = 0;
     for (int k : order) {
         const FastBlock& f = fbs[k];
-        if (f.bb.n == 0) continue;
+        if (f.bb.n == 0 || f.bb.strategy == BN_STRATEGY_SORT) continue;  // sort blocks: own launches
         const int64_t parts = (f.bb.n + f.bb.tile - 1) / f.bb.tile;
         for (int64_t j = 0; j < parts; ++j) items[ni++] = make_int4(k, (int)j, 0, 0);
     }
@@ -244,8 +244,27 @@ static void fill_plan(std::vector<FastBlock>& fbs, const PlanLayout& L, unsigned
 static int count_items(const std::vector<FastBlock>& fbs) {
     int64_t ni = 0;
     for (const FastBlock& f : fbs)
-        if (f.bb.n > 0) ni += (f.bb.n + f.bb.tile - 1) / f.bb.tile;
+        if (f.bb.n > 0 && f.bb.strategy != BN_STRATEGY_SORT) ni += (f.bb.n + f.bb.tile - 1) / f.bb.tile;
     return (int)ni;
+}
+
+// BinArgs of a block that takes the bucketed sort path. The mesh descriptor
+// goes by value; its f64 edge keys point into the batch plan's memory, which
+// the prepare launch fills first.
+static BinArgs sort_args(const FastBlock& f, int dtype, int n_attrs, int sum_mode) {
+    BinArgs a;
+    memset(&a, 0, sizeof a);
+    a.dtype = dtype;
+    a.n_attrs = n_attrs;
+    a.sum_mode = sum_mode;
+    a.x = f.bb.x;
+    a.y = f.bb.y;
+    for (int k = 0; k < n_attrs; ++k) a.a[k] = f.bb.a[k];
+    a.n = f.bb.n;
+    a.grid = f.bb.g;
+    a.dev_grid = nullptr;
+    a.st = f.bb.st;
+    return a;
 }
 
 // Time one block alone with one strategy (autotuner trial), on the context
@@ -272,12 +291,26 @@ static float trial(bn_context* c, FastBlock f, int strategy, int aggregate, int 
         unsigned char* d = static_cast<unsigned char*>(dev);
         const KernelCtx kc{c->stream, c->num_sms, c->smem_optin, nullptr};
         cudaError_t e = cudaMemcpyAsync(dev, host, L.bytes, cudaMemcpyHostToDevice, c->stream);
+        SortDesc sd;
+        void* sort_scratch = nullptr;
+        BinArgs sa;
+        if (strategy == BN_STRATEGY_SORT) {
+            sa = sort_args(one[0], dtype, n_attrs, sum_mode);
+            if (!sort_plan(sa, c->smem_optin, &sd) ||
+                cudaMallocAsync(&sort_scratch, sort_scratch_bytes(sd, sa), c->stream) != cudaSuccess)
+                e = cudaErrorInvalidValue;
+        }
         auto run = [&]() {
-            return queue_batch(kc, dtype, sum_mode, n_attrs, reinterpret_cast<BatchBlock*>(d + L.off_blocks),
-                               reinterpret_cast<int64_t*>(d + L.off_bin_start),
-                               reinterpret_cast<int64_t*>(d + L.off_edge_start),
-                               reinterpret_cast<int4*>(d + L.off_items), reinterpret_cast<int*>(d + L.off_counter),
-                               1, ni, bins, edges, smem, want_avg);
+            cudaError_t e2 = queue_batch(kc, dtype, sum_mode, n_attrs, reinterpret_cast<BatchBlock*>(d + L.off_blocks),
+                                         reinterpret_cast<int64_t*>(d + L.off_bin_start),
+                                         reinterpret_cast<int64_t*>(d + L.off_edge_start),
+                                         reinterpret_cast<int4*>(d + L.off_items), reinterpret_cast<int*>(d + L.off_counter),
+                                         1, ni, bins, edges, smem, false);
+            if (e2 == cudaSuccess && strategy == BN_STRATEGY_SORT) e2 = launch_bin_sort(kc, sa, sd, sort_scratch);
+            if (e2 == cudaSuccess && want_avg)
+                e2 = launch_batch_finalize(kc, reinterpret_cast<BatchBlock*>(d + L.off_blocks),
+                                           reinterpret_cast<int64_t*>(d + L.off_bin_start), 1, bins);
+            return e2;
         };
         if (e == cudaSuccess) e = run();  // untimed: the first launch also loads the module
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
@@ -285,6 +318,7 @@ static float trial(bn_context* c, FastBlock f, int strategy, int aggregate, int 
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (sort_scratch) cudaFreeAsync(sort_scratch, c->stream);
     }
     cudaFreeAsync(dev, c->stream);
     cudaStreamSynchronize(c->stream);
@@ -372,7 +406,11 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
         if (forced == BN_STRATEGY_PRIVATE) {
             if (!fits) return fail(BN_ERR_INVALID_ARG, "bn_bin_batch: block %d mesh does not fit shared memory", k);
             ch.strategy = BN_STRATEGY_PRIVATE;
-        } else if (forced == BN_STRATEGY_GLOBAL || forced == BN_STRATEGY_SORT) {
+        } else if (forced == BN_STRATEGY_SORT) {
+            SortDesc probe;
+            ch.strategy = (f.bb.n > 0 && sort_plan(sort_args(f, dtype, A, sum_mode), c->smem_optin, &probe))
+                              ? BN_STRATEGY_SORT : BN_STRATEGY_GLOBAL;
+        } else if (forced == BN_STRATEGY_GLOBAL) {
             ch.strategy = BN_STRATEGY_GLOBAL;
         } else {
             std::lock_guard<std::mutex> lk(cache.mu);
@@ -382,17 +420,37 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
                 if (ch.strategy == BN_STRATEGY_PRIVATE && !fits) ch.strategy = BN_STRATEGY_GLOBAL;
             } else if (f.bb.n > 0) {
                 float best = -1.0f;
-                const int cands[3][2] = {{BN_STRATEGY_PRIVATE, 0}, {BN_STRATEGY_GLOBAL, 0}, {BN_STRATEGY_GLOBAL, 1}};
+                SortDesc probe;
+                const bool sort_fits = f.bb.n >= 4 * (int64_t)c->num_sms * 1024 &&
+                                       sort_plan(sort_args(f, dtype, A, sum_mode), c->smem_optin, &probe) &&
+                                       probe.nb >= 8;
+                const int cands[4][2] = {{BN_STRATEGY_PRIVATE, 0}, {BN_STRATEGY_GLOBAL, 0}, {BN_STRATEGY_GLOBAL, 1},
+                                         {BN_STRATEGY_SORT, 0}};
+                std::string times;
                 for (auto& cd : cands) {
                     if (cd[0] == BN_STRATEGY_PRIVATE && !fits) continue;
+                    if (cd[0] == BN_STRATEGY_SORT && !sort_fits) continue;
                     const float ms = trial(c, f, cd[0], cd[1], dtype, sum_mode, A,
                                            cd[0] == BN_STRATEGY_PRIVATE ? mesh : 0, want_avg);
+                    char tb[64];
+                    snprintf(tb, sizeof tb, " %s%s=%.3fms",
+                             cd[0] == BN_STRATEGY_PRIVATE ? "private" : cd[0] == BN_STRATEGY_SORT ? "sort" : "global",
+                             cd[0] == BN_STRATEGY_GLOBAL && cd[1] ? "+agg" : "", ms);
+                    times += tb;
                     if (ms >= 0.0f && (best < 0.0f || ms < best)) {
                         best = ms;
                         ch = Choice{cd[0], cd[1]};
                     }
                 }
                 cache.choices[f.cls] = ch;
+                char head[128];
+                snprintf(head, sizeof head, "batch dtype=%s attrs=%d bins=2^%d n=2^%d:", dtype == BN_F64 ? "f64" : "f32",
+                         A, f.cls.lb, f.cls.ln);
+                std::lock_guard<std::mutex> lk2(c->tune_mu);
+                c->tune_log.push_back(std::string(head) + times + " -> " +
+                                      (ch.strategy == BN_STRATEGY_PRIVATE ? "private"
+                                       : ch.strategy == BN_STRATEGY_SORT ? "sort"
+                                       : ch.aggregate ? "global+agg" : "global"));
             }
         }
         if (agg == BN_AGG_ON) ch.aggregate = 1;
@@ -428,7 +486,10 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
         for (auto& g : cache.graphs)
             if (g->shape == shape) G = g.get();
     }
-    const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy;
+    int ni = n_items;
+    int64_t bins = 0, edges = 0;
+    for (const FastBlock& f : fbs) bins += f.bins;
+    edges = total_edges;
     if (!G) {
         std::unique_ptr<BatchGraph> ng(new BatchGraph());
         ng->shape = shape;
@@ -436,8 +497,6 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
         if (e == cudaSuccess) e = cudaHostAlloc(&ng->host, L.bytes, cudaHostAllocDefault);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ng->last, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: plan memory");
-        int ni;
-        int64_t bins, edges;
         fill_plan(fbs, L, static_cast<unsigned char*>(ng->host), static_cast<unsigned char*>(ng->dev), &ni,
                   &bins, &edges, dtype);
         ng->h_blocks = reinterpret_cast<BatchBlock*>(static_cast<unsigned char*>(ng->host) + L.off_blocks);
@@ -445,42 +504,10 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
         // the static part (starts, items) goes over once
         e = cudaMemcpy(ng->dev, ng->host, L.bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: plan upload");
-        unsigned char* d = static_cast<unsigned char*>(ng->dev);
-        std::atomic<uint64_t> nlaunch{0};
-        const KernelCtx kc{c->stream, c->num_sms, c->smem_optin, &nlaunch};
-        auto body = [&]() {
-            cudaError_t e2 = cudaMemcpyAsync(ng->d_blocks, ng->h_blocks, sizeof(BatchBlock) * n_blocks,
-                                             cudaMemcpyHostToDevice, c->stream);
-            if (e2 == cudaSuccess)
-                e2 = queue_batch(kc, dtype, sum_mode, A, ng->d_blocks, reinterpret_cast<int64_t*>(d + L.off_bin_start),
-                                 reinterpret_cast<int64_t*>(d + L.off_edge_start),
-                                 reinterpret_cast<int4*>(d + L.off_items), reinterpret_cast<int*>(d + L.off_counter),
-                                 n_blocks, ni, bins, edges, smem, want_avg);
-            return e2;
-        };
-        if (capturable) {
-            cudaGraph_t graph = nullptr;
-            e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-            cudaError_t eb = e == cudaSuccess ? body() : e;
-            cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
-            if (e == cudaSuccess) e = eb != cudaSuccess ? eb : ee;
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&ng->exec, graph, 0);
-            if (graph) cudaGraphDestroy(graph);
-            if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: graph capture");
-            ng->launches = nlaunch.load();
-        }
         std::lock_guard<std::mutex> lk(cache.mu);
         cache.graphs.push_back(std::move(ng));
         if (cache.graphs.size() > 8) cache.graphs.erase(cache.graphs.begin());
         G = cache.graphs.back().get();
-        if (!capturable) {
-            // no graph on the legacy stream: launch directly
-            cudaError_t e2 = body();
-            if (e2 != cudaSuccess) return cuda_fail(e2, "bn_bin_batch: launch");
-            c->launches.fetch_add(nlaunch.load());
-            cudaEventRecord(G->last, c->stream);
-            return BN_OK;
-        }
     } else {
         // same shape: wait until the pinned descriptors are free, rewrite them
         cudaEventSynchronize(G->last);
@@ -496,6 +523,72 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
             }
             reinterpret_cast<BatchBlock*>(host + L.off_blocks)[k] = f.bb;
         }
+    }
+
+    // blocks on the sort path: their scratch and arguments change per call
+    struct SortJob {
+        BinArgs a;
+        SortDesc sd;
+        void* scratch;
+    };
+    std::vector<SortJob> sorts;
+    for (const FastBlock& f : fbs) {
+        if (f.bb.strategy != BN_STRATEGY_SORT || f.bb.n == 0) continue;
+        SortJob j;
+        j.a = sort_args(f, dtype, A, sum_mode);
+        if (!sort_plan(j.a, c->smem_optin, &j.sd)) return fail(BN_ERR_INTERNAL, "bn_bin_batch: sort plan changed");
+        j.scratch = plan.alloc(sort_scratch_bytes(j.sd, j.a));
+        if (!j.scratch) return cuda_fail(plan.err, "bn_bin_batch: sort scratch");
+        sorts.push_back(j);
+    }
+
+    unsigned char* d = static_cast<unsigned char*>(G->dev);
+    std::atomic<uint64_t> nlaunch{0};
+    const KernelCtx kc{c->stream, c->num_sms, c->smem_optin, &nlaunch};
+    auto body = [&]() {
+        cudaError_t e2 = cudaMemcpyAsync(G->d_blocks, G->h_blocks, sizeof(BatchBlock) * n_blocks,
+                                         cudaMemcpyHostToDevice, c->stream);
+        if (e2 == cudaSuccess)
+            e2 = queue_batch(kc, dtype, sum_mode, A, G->d_blocks, reinterpret_cast<int64_t*>(d + L.off_bin_start),
+                             reinterpret_cast<int64_t*>(d + L.off_edge_start),
+                             reinterpret_cast<int4*>(d + L.off_items), reinterpret_cast<int*>(d + L.off_counter),
+                             n_blocks, ni, bins, edges, smem, false);
+        for (SortJob& j : sorts)
+            if (e2 == cudaSuccess) e2 = launch_bin_sort(kc, j.a, j.sd, j.scratch);
+        if (e2 == cudaSuccess && want_avg)
+            e2 = launch_batch_finalize(kc, G->d_blocks, reinterpret_cast<int64_t*>(d + L.off_bin_start), n_blocks, bins);
+        return e2;
+    };
+    const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy;
+    if (!capturable) {
+        // no graph on the legacy stream: launch directly
+        cudaError_t e2 = body();
+        if (e2 != cudaSuccess) return cuda_fail(e2, "bn_bin_batch: launch");
+        c->launches.fetch_add(nlaunch.load());
+        cudaEventRecord(G->last, c->stream);
+        return BN_OK;
+    }
+    if (!G->exec || !sorts.empty()) {
+        // capture; a graph with sort blocks is re-captured every call (their
+        // kernel arguments carry this call's pointers) and the executable
+        // graph updated in place
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        cudaError_t eb = e == cudaSuccess ? body() : e;
+        cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+        if (e == cudaSuccess) e = eb != cudaSuccess ? eb : ee;
+        if (e == cudaSuccess && G->exec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(G->exec, graph, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(G->exec);
+                G->exec = nullptr;
+            }
+        }
+        if (e == cudaSuccess && !G->exec) e = cudaGraphInstantiate(&G->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: graph capture");
+        G->launches = nlaunch.load();
     }
     cudaError_t e = cudaGraphLaunch(G->exec, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: graph launch");

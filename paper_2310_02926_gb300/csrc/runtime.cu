@@ -736,7 +736,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         if (private_smem_bytes(args, c->smem_optin) > 0) cands.push_back({BN_STRATEGY_PRIVATE, 0});
         cands.push_back({BN_STRATEGY_GLOBAL, 0});
         cands.push_back({BN_STRATEGY_GLOBAL, 1});
-        if (sort_scratch) cands.push_back({BN_STRATEGY_SORT, 0});
+        if (sort_scratch && sortd.nb >= 8) cands.push_back({BN_STRATEGY_SORT, 0});  // a few buckets: pointless
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         float best = -1.0f;
         Cand win{strat, args.aggregate};
