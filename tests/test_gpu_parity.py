@@ -496,6 +496,44 @@ def test_server_results_equal_alone(bn, ctx):
         check(w, g, TOL_F32C)
 
 
+@pytest.mark.parametrize("inputs", ["host", "device_tight_budget", "strided"])
+def test_server_staging_paths(bn, ctx, inputs):
+    """Requests whose columns are on the host, or that arrive while the budget
+    is used up (deep copy to pinned host memory, admitted later), or whose
+    columns are strided: every result equals binning the block alone."""
+    rng = np.random.default_rng(61)
+    n_req = 12
+    sizes = rng.integers(20_000, 120_000, n_req)
+    side = 48
+    budget = 6 << 20 if inputs == "device_tight_budget" else 1 << 30
+    srv = bn.bn_server_create(ctx.handle, budget, max_inflight=2, max_batch=3)
+    reqs = []
+    for i in range(n_req):
+        w = workloads.plummer(int(sizes[i]), seed=100 + i, dtype=np.float32, res=side)
+        w.attrs[2] = np.abs(w.attrs[2])
+        if inputs == "host":
+            cols = [torch.from_numpy(c) for c in (w.x, w.y, *w.attrs)]
+        elif inputs == "strided":
+            aos = torch.from_numpy(np.stack([w.x, w.y, *w.attrs], axis=1)).cuda()
+            cols = [aos[:, k] for k in range(aos.shape[1])]
+        else:
+            cols = [torch.from_numpy(c).cuda() for c in (w.x, w.y, *w.attrs)]
+        o = bn.alloc_outputs(3, side * side, torch.float32, torch.device("cuda"))
+        r = bn.result_struct(o)
+        blk = bn.block(cols[0], cols[1], cols[2:], bn.grid(w.lo, w.hi, w.res), r)
+        reqs.append((bn.bn_server_submit(srv, blk, bn.OP_ALL), o, r, blk, cols, w))
+    for req, *_ in reqs:
+        assert bn.bn_wait(req, 60_000_000) == bn.OK
+        bn.bn_request_release(req)
+    stats = bn.bn_server_stats_get(srv)
+    bn.bn_server_destroy(srv)
+    assert stats["completed"] == n_req and stats["failed"] == 0
+    if inputs == "device_tight_budget":
+        assert stats["peak_bytes"] <= budget
+    for req, o, r, blk, cols, w in reqs:
+        check(w, to_numpy_result(o), TOL_F32C, label=f"{inputs} {w.n}")
+
+
 def test_server_rejects_over_budget(bn, ctx):
     x = torch.zeros(1 << 20, dtype=torch.float32, device="cuda")
     o = bn.alloc_outputs(0, 16, torch.float32, torch.device("cuda"), ops=bn.OP_COUNT)
