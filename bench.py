@@ -22,9 +22,7 @@ Multi-GPU (torchrun): every rank bins its own replica of the workload
 from __future__ import annotations
 
 import argparse
-import csv
 import hashlib
-import io
 import json
 import os
 import statistics
@@ -505,6 +503,8 @@ def main():
     ap.add_argument("--serving-priority", default="high", choices=["low", "high"],
                     help="stream priority of the server relative to the producer")
     ap.add_argument("--no-producer", action="store_true", help="serving without the producer")
+    ap.add_argument("--ops", default="all", choices=["all", "count", "count+sum", "count+minmax"],
+                    help="reductions to compute (all = count/sum/min/max/avg, the benchmark's)")
     ap.add_argument("--check", action="store_true",
                     help="compare the last step with the CPU oracle and report per-bin errors")
     args = ap.parse_args()
@@ -546,11 +546,15 @@ def main():
     ctx = bn.Context(local, stream=stream.cuda_stream, profile=True)
     flags = {"auto": 0, "global": bn.STRATEGY_GLOBAL, "private": bn.STRATEGY_PRIVATE,
              "sort": bn.STRATEGY_SORT}[args.strategy]
-    ops = bn.OP_ALL | flags | {"f32c": bn.SUM_F32C, "f32": bn.SUM_F32, "f64": bn.SUM_F64}[args.sum]
+    op_bits = {"all": bn.OP_ALL, "count": bn.OP_COUNT, "count+sum": bn.OP_COUNT | bn.OP_SUM,
+               "count+minmax": bn.OP_COUNT | bn.OP_MIN | bn.OP_MAX}[args.ops]
+    ops = op_bits | flags | {"f32c": bn.SUM_F32C, "f32": bn.SUM_F32, "f64": bn.SUM_F64}[args.sum]
+    if args.ops != "all":
+        args.check = False
     g = bn.grid(w.lo, w.hi, w.res)
     torch.cuda.synchronize(dev)
     with torch.cuda.stream(stream):
-        out = bn.alloc_outputs(N_ATTR, B, tdtype, dev)
+        out = bn.alloc_outputs(N_ATTR, B, tdtype, dev, ops=op_bits)
         res_struct = bn.result_struct(out)
 
         def step():
@@ -606,11 +610,9 @@ def main():
     e2e = None
     if args.e2e_steps > 0 and rank == 0:
         hcols = [torch.from_numpy(c).pin_memory() for c in (w.x, w.y, *w.attrs)]
-        hout = bn.alloc_outputs(N_ATTR, B, tdtype, torch.device("cpu"))
-        for k in ("count",):
-            hout[k] = hout[k].pin_memory()
-        for k in ("sum", "min", "max", "avg"):
-            hout[k] = [t.pin_memory() for t in hout[k]]
+        hout = bn.alloc_outputs(N_ATTR, B, tdtype, torch.device("cpu"), ops=op_bits)
+        for k in list(hout):
+            hout[k] = [t.pin_memory() for t in hout[k]] if isinstance(hout[k], list) else hout[k].pin_memory()
         ctx.bin_particles(hcols[0], hcols[1], hcols[2:], w.lo, w.hi, w.res, ops=ops, out=hout)
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
@@ -637,7 +639,7 @@ def main():
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dt_label, "data": "synthetic",
             "config": dict(workload_config(args.workload, N_PART, bytes_in), strategy=strategy,
-                           autotuner=tuning,
+                           autotuner=tuning, ops=args.ops,
                            sum_mode=args.sum if dt_label == "f32" else "f64",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
             "hbm_frac_step": step_gbs / hbm,

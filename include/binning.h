@@ -272,7 +272,9 @@ BN_API bn_status bn_context_profile(bn_context* ctx, double* total_ms, uint64_t*
  *   x, y, attrs[0..n_attrs)  same n and dtype (BN_F32 or BN_F64); device
  *                            buffers are read in place (zero copy), host
  *                            buffers are staged to the device
- *   n_attrs                  0..BN_MAX_ATTR (0: count only)
+ *   n_attrs                  0..BN_MAX_ATTR (0: count only); when `ops`
+ *                            selects no sum, avg, min or max the columns are
+ *                            validated but neither staged nor read
  *   out                      see bn_result; must not be NULL
  *   sync                     1: return after completion (status of the work);
  *                            0: return at once, the work runs asynchronously

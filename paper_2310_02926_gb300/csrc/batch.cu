@@ -331,12 +331,14 @@ static float trial(bn_context* c, FastBlock f, int strategy, int aggregate, int 
 static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks, uint32_t ops,
                             bn_request* r, Plan& plan) {
     const int dtype = blocks[0].x.dtype;
-    const int A = blocks[0].n_attrs;
     const uint32_t sum_bits = ops & BN_SUM_MASK;
     const int sum_mode = dtype == BN_F64 ? kSumF64 : sum_bits == BN_SUM_F32 ? kSumF32
                                                    : sum_bits == BN_SUM_F64 ? kSumF64 : kSumF32C;
     const bool want_avg = ops & BN_OP_AVG, want_sum = ops & BN_OP_SUM;
     const bool want_min = ops & BN_OP_MIN, want_max = ops & BN_OP_MAX, want_count = ops & BN_OP_COUNT;
+    // attribute columns are validated; with no per-attribute op they are not read
+    const int A_in = blocks[0].n_attrs;
+    const int A = (want_sum || want_avg || want_min || want_max) ? A_in : 0;
     const uint32_t forced = ops & BN_STRATEGY_MASK;
     const uint32_t agg = ops & BN_AGG_MASK;
     if (ops & BN_OP_ACCUMULATE) return fail(BN_ERR_INVALID_ARG, "bn_bin_batch: accumulate is not supported for batches");
@@ -350,7 +352,7 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
         const int64_t n = b.x.n;
         bn_status st = validate_buffer(c, &b.x, n, dtype, "x");
         if (st == BN_OK) st = validate_buffer(c, &b.y, n, dtype, "y");
-        for (int a = 0; a < A && st == BN_OK; ++a) st = validate_buffer(c, &b.attrs[a], n, dtype, "attr");
+        for (int a = 0; a < A_in && st == BN_OK; ++a) st = validate_buffer(c, &b.attrs[a], n, dtype, "attr");
         if (st == BN_OK) st = make_grid_desc(&b.grid, dtype, &f.bb.g);
         if (st != BN_OK) return fail(st, "bn_bin_batch: block %d: %s", k, bn_last_error());
         for (int a = 0; a < 2; ++a) {

@@ -24,8 +24,8 @@ struct AxisDesc {
     int32_t closed;
     // f64 coordinates only: 1 when the FP32 estimate of t is within `delta`
     // bins of the exact t everywhere on the axis, with delta < 1/4 (then the
-    // estimate plus the edge-key correction below is exact); 0 = evaluate the
-    // reference sequence on the FP64 pipe.
+    // estimate plus the edge-key correction below is exact); 0 = the
+    // estimate only seeds a search of the edge keys.
     int32_t fast;
     float delta;
 };
@@ -77,9 +77,19 @@ struct StateDesc {
 __device__ __forceinline__ bool is_nan_bits(float v) {
     return (__float_as_uint(v) & 0x7fffffffu) > 0x7f800000u;
 }
+// The f64 test is spelled in PTX so that it stays two integer instructions:
+// written in C, the compiler may turn it into an unordered FP64 compare, which
+// runs on GB300's narrow FP64 pipe and, being side-effect free, can be hoisted
+// out of the branches that need it into every particle's path.
 __device__ __forceinline__ bool is_nan_bits(double v) {
-    return ((unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull) >
-           0x7ff0000000000000ull;
+    unsigned int r;
+    asm("{\n\t.reg .pred p;\n\t.reg .b64 m;\n\t"
+        "and.b64 m, %1, 0x7fffffffffffffff;\n\t"
+        "setp.gt.u64 p, m, 0x7ff0000000000000;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "l"(__double_as_longlong(v)));
+    return r != 0;
 }
 
 // Ordered integer key of an IEEE value: key(a) < key(b) iff a < b for
@@ -169,24 +179,31 @@ __device__ __forceinline__ Axis<T> make_axis(const AxisDesc& d) {
     return a;
 }
 
+// Nearest integer of t (0 <= t < 2^22) with plain round-to-nearest FP32 adds
+// and integer operations only. GB300 runs float-to-integer conversions and
+// rounding instructions on its narrow FP64 pipe; here, adding 1.5 * 2^23
+// (bits 0x4B400000) lands in [2^23, 2^24) where the ulp is 1, so the sum is
+// 1.5 * 2^23 + round(t) exactly and its low bits are round(t). *d receives
+// t - round(t), exact (Sterbenz, or t itself when the rounded value is 0),
+// with |d| <= 1/2.
+__device__ __forceinline__ int round_small(float t, float* d) {
+    const float s = __fadd_rn(t, 12582912.0f);
+    *d = __fsub_rn(t, __fsub_rn(s, 12582912.0f));
+    return __float_as_int(s) - 0x4B400000;
+}
+
 // The reference sequence (Sec. 4.2 bin location, rounding fixed as
-// t = RN(RN(x - lo) * s), i = min(trunc(t), res - 1)), in f32.
+// t = RN(RN(x - lo) * s), i = min(trunc(t), res - 1)), in f32. Inside the
+// mesh t >= 0 (t is -0 only when x = -0 and lo = +0) and t is within a few
+// ulps of at most res <= 65536 < 2^22, so trunc(t) = floor(t), taken from
+// round_small.
 __device__ __forceinline__ int axis_bin(const Axis<float>& a, float x) {
     bool inside = a.closed ? (a.lo <= x && x <= a.hi) : (a.lo <= x && x < a.hi);
     if (!inside) return -1;
     float t = __fmul_rn(__fsub_rn(x, a.lo), a.s);
-    int k = __float2int_rz(t);
-    return min(k, a.res - 1);
-}
-
-// Same sequence for f64, evaluated directly on the FP64 pipe.
-__device__ __forceinline__ int axis_bin_direct(double lo, double hi, double s, int res,
-                                               bool closed, double x) {
-    bool inside = closed ? (lo <= x && x <= hi) : (lo <= x && x < hi);
-    if (!inside) return -1;
-    double t = __dmul_rn(__dsub_rn(x, lo), s);
-    int k = __double2int_rz(t);
-    return min(k, res - 1);
+    float d;
+    const int r = round_small(t, &d);
+    return min(d < 0.0f ? r - 1 : r, a.res - 1);  // floor; t = -0 gives d = -0, not < 0
 }
 
 // Inverse of ordered_key(double).
@@ -204,13 +221,26 @@ __host__ __device__ __forceinline__ double key_to_double(long long k) {
 // FP32 approximation of a double from its top 32 bits, integer pipe only:
 // the magnitude is truncated to 20 mantissa bits (relative error < 2^-20);
 // |x| < 2^-126 becomes +/-0 and |x| >= 2^128 becomes +/-inf.
+// Spelled in PTX for the same reason as is_nan_bits(double): the range tests
+// on the high word must not become FP64 compares. Exponent bias change:
+// 896 << 20 = 0x38000000; 897 << 20 = 0x38100000; 1151 << 20 = 0x47F00000.
 __device__ __forceinline__ float approx_float(double x) {
-    unsigned int hi32 = (unsigned int)((unsigned long long)__double_as_longlong(x) >> 32);
-    unsigned int mag = hi32 & 0x7fffffffu;
-    unsigned int sign = hi32 & 0x80000000u;
-    if (mag < (897u << 20)) return __uint_as_float(sign);
-    if (mag >= (1151u << 20)) return __uint_as_float(sign | 0x7f800000u);
-    return __uint_as_float(sign | ((mag - (896u << 20)) << 3));
+    unsigned int r;
+    asm("{\n\t.reg .b32 lo, hi, mag, sgn, v, w;\n\t.reg .pred p, q;\n\t"
+        "mov.b64 {lo, hi}, %1;\n\t"
+        "and.b32 mag, hi, 0x7fffffff;\n\t"
+        "and.b32 sgn, hi, 0x80000000;\n\t"
+        "sub.u32 v, mag, 0x38000000;\n\t"
+        "shl.b32 v, v, 3;\n\t"
+        "or.b32 v, v, sgn;\n\t"
+        "setp.lt.u32 p, mag, 0x38100000;\n\t"
+        "selp.b32 v, sgn, v, p;\n\t"
+        "setp.ge.u32 q, mag, 0x47F00000;\n\t"
+        "or.b32 w, sgn, 0x7f800000;\n\t"
+        "selp.b32 %0, w, v, q;\n\t}"
+        : "=r"(r)
+        : "l"(__double_as_longlong(x)));
+    return __uint_as_float(r);
 }
 
 // f64 axis for the exact edge-key method. idx(x) = min(trunc(RN(RN(x-lo)*s)),
@@ -219,34 +249,32 @@ __device__ __forceinline__ float approx_float(double x) {
 // idx >= i (E[0] = key(lo); E[res] = key(hi), plus one when closed). The
 // kernel estimates i in FP32, then moves it by at most one bin so that
 // E[i] <= key(x) < E[i+1]: the same index as the reference sequence, with
-// no FP64 arithmetic.
+// no FP64 arithmetic. Every f64 axis has its edge keys, so this is the only
+// per-particle path: when the estimate's error is not proven below 1/4 bin
+// (huge coordinates or scales), the estimate only seeds the search. (A
+// branch into an FP64 evaluation here would cost every particle: the
+// compiler hoists parts of it out of the branch, onto the FP64 pipe.)
 struct AxisF64 {
-    const long long* E;
+    const long long* E;  // res + 1 edge keys
     long long klo, khi;  // E[0], E[res]
     float flo, fs;       // FP32 estimate parameters
-    float delta;         // bound on |estimate - t|, in bins
+    float delta;         // bound on |estimate - t| in bins; +inf if unproven
     float tmax;          // res - delta
+    float tlast;         // res - 1
     int res;
-    bool fast;
-    double lo, hi, s;
-    bool closed;
 };
 
 __device__ __forceinline__ AxisF64 make_axis_f64(const AxisDesc& d, const long long* E) {
     AxisF64 a;
     a.E = E;
     a.res = d.res;
-    a.fast = d.fast != 0 && E != nullptr;
-    a.lo = d.lo;
-    a.hi = d.hi;
-    a.s = d.s;
-    a.closed = d.closed != 0;
     a.flo = approx_float(d.lo);
-    a.fs = (float)d.s;
-    a.delta = d.delta;
-    a.tmax = (float)d.res - d.delta;
-    a.klo = a.fast ? __ldg(E) : 0;
-    a.khi = a.fast ? __ldg(E + d.res) : 0;
+    a.fs = (float)d.s;  // may round to inf when !fast; the search handles it
+    a.delta = d.fast ? d.delta : __int_as_float(0x7f800000);
+    a.tmax = (float)d.res - a.delta;
+    a.tlast = (float)(d.res - 1);
+    a.klo = __ldg(E);
+    a.khi = __ldg(E + d.res);
     return a;
 }
 
@@ -254,19 +282,25 @@ __device__ __forceinline__ AxisF64 make_axis_f64(const AxisDesc& d, const long l
 // t_f is within delta of the reference t, so when t_f lies in
 // (delta, res - delta) and at least delta away from the nearest integer,
 // x is inside and trunc(t) == trunc(t_f). Otherwise (about 2 * delta of the
-// particles, and every particle outside or near the ends) the ordered key
-// of x is compared with the exact edge keys.
+// particles, every particle outside or near the ends, and every particle of
+// an axis without a proven delta) the ordered key of x is compared with the
+// exact edge keys, starting from the estimate.
 __device__ __forceinline__ int axis_bin(const AxisF64& a, double x) {
-    if (!a.fast) return axis_bin_direct(a.lo, a.hi, a.s, a.res, a.closed, x);
     const float t = __fmul_rn(__fsub_rn(approx_float(x), a.flo), a.fs);
-    if (t > a.delta && t < a.tmax) {
-        const float fl = truncf(t);
-        const float fr = t - fl;  // exact: t and fl share the binade
-        if (fr > a.delta && fr < 1.0f - a.delta) return (int)fl;
+    if (t > a.delta && t < a.tmax) {  // then 0 < t < res <= 65536
+        // t is more than delta from every integer iff |t - round(t)| > delta
+        // (delta < 1/4), and then trunc(t) = floor(t) = round(t) - (d < 0)
+        float d;
+        const int r = round_small(t, &d);
+        if (fabsf(d) > a.delta) return d < 0.0f ? r - 1 : r;
     }
     const long long k = ordered_key(x);
     if (k < a.klo || k >= a.khi) return -1;  // NaN keys fall outside too
-    int i = (t > 0.0f) ? __float2int_rz(t) : 0;
+    // seed: floor of the estimate clamped to [0, res - 1] (fmaxf maps NaN to 0)
+    float d;
+    const float tc = fminf(fmaxf(t, 0.0f), a.tlast);
+    const int r = round_small(tc, &d);
+    int i = d < 0.0f ? r - 1 : r;
     i = max(0, min(i, a.res - 1));
     if (k < __ldg(a.E + i)) {
         i -= 1;
@@ -275,8 +309,8 @@ __device__ __forceinline__ int axis_bin(const AxisF64& a, double x) {
     }
     i = max(0, min(i, a.res - 1));
     if (k < __ldg(a.E + i) || k >= __ldg(a.E + i + 1)) {
-        // Not expected when `fast` holds; binary search keeps the result exact.
-        int lo = 0, hi = a.res;  // E[lo] <= k < E[hi]
+        // the seed was more than one bin off: binary search, E[lo] <= k < E[hi]
+        int lo = 0, hi = a.res;
         while (hi - lo > 1) {
             int mid = (lo + hi) >> 1;
             if (k >= __ldg(a.E + mid)) lo = mid; else hi = mid;

@@ -235,6 +235,7 @@ template <typename T, int MODE>
 static cudaError_t dispatch_batch(const KernelCtx& kc, const BatchBlock* blocks, const int4* items,
                                   int n_items, int* counter, int n_attrs, size_t smem) {
     switch (n_attrs) {
+        case 0: return launch_batch_bin_t<T, 0, MODE>(kc, blocks, items, n_items, counter, n_attrs, smem);
         case 1: return launch_batch_bin_t<T, 1, MODE>(kc, blocks, items, n_items, counter, n_attrs, smem);
         case 2: return launch_batch_bin_t<T, 2, MODE>(kc, blocks, items, n_items, counter, n_attrs, smem);
         case 3: return launch_batch_bin_t<T, 3, MODE>(kc, blocks, items, n_items, counter, n_attrs, smem);

@@ -228,6 +228,7 @@ static cudaError_t launch_global_t(const KernelCtx& kc, const BinArgs& a) {
 template <typename T>
 static cudaError_t dispatch_global(const KernelCtx& kc, const BinArgs& a) {
     switch (a.n_attrs) {
+        case 0: return launch_global_t<T, 0>(kc, a);
         case 1: return launch_global_t<T, 1>(kc, a);
         case 2: return launch_global_t<T, 2>(kc, a);
         case 3: return launch_global_t<T, 3>(kc, a);

@@ -197,6 +197,7 @@ static cudaError_t launch_private_t(const KernelCtx& kc, const BinArgs& a, size_
 template <typename T, int MODE>
 static cudaError_t dispatch_a(const KernelCtx& kc, const BinArgs& a, size_t smem) {
     switch (a.n_attrs) {
+        case 0: return launch_private_t<T, 0, MODE>(kc, a, smem);
         case 1: return launch_private_t<T, 1, MODE>(kc, a, smem);
         case 2: return launch_private_t<T, 2, MODE>(kc, a, smem);
         case 3: return launch_private_t<T, 3, MODE>(kc, a, smem);

@@ -420,6 +420,7 @@ static cudaError_t launch_sort_t(const KernelCtx& kc, const BinArgs& a, const So
 template <typename T, int MODE>
 static cudaError_t dispatch_sort(const KernelCtx& kc, const BinArgs& a, const SortDesc& sd) {
     switch (a.n_attrs) {
+        case 0: return launch_sort_t<T, 0, MODE>(kc, a, sd);
         case 1: return launch_sort_t<T, 1, MODE>(kc, a, sd);
         case 2: return launch_sort_t<T, 2, MODE>(kc, a, sd);
         case 3: return launch_sort_t<T, 3, MODE>(kc, a, sd);

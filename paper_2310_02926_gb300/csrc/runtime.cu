@@ -585,6 +585,9 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         return fail(BN_ERR_INVALID_ARG, "BN_OP_ACCUMULATE needs count, sum, min and max");
     if (accumulate && grid->auto_bounds)
         return fail(BN_ERR_INVALID_ARG, "BN_OP_ACCUMULATE needs explicit bounds");
+    // the attribute columns were validated above; with no per-attribute
+    // operation requested they are neither staged nor read
+    if (!want_sum && !want_avg && !want_min && !want_max) n_attrs = 0;
 
     BinArgs args;
     memset(&args, 0, sizeof args);

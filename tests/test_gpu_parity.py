@@ -196,6 +196,8 @@ F64_GRIDS = [
     ((0.0, 0.0), (1.0, 1.0), (3, 7)),
     ((1e6, -3.0), (1e6 + 1.0, 3.0), (1000, 3)),    # too fine for the FP32 estimate
     ((-1e-3, 5.0), (2e-3, 5.0 + 1e-9), (999, 17)),
+    ((1e300, -1e300), (2e300, 1e300), (16, 9)),     # FP32 estimate overflows: search only
+    ((1e-300, 0.0), (2e-300, 1.0), (5, 5)),         # bin width below FP32 range
 ]
 
 
