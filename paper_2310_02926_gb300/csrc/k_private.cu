@@ -20,8 +20,12 @@
 
 namespace bn {
 
-template <typename T, int A_CT, int MODE>
-__global__ void __launch_bounds__(512) k_bin_private(BinArgs args, int64_t head, int64_t groups) {
+// NT threads per CTA: 512 when two or more CTAs fit on an SM; 1024 (at most
+// 64 registers, one vector group per pipeline stage) when the mesh leaves
+// room for one CTA only, so that an SM still has 32 warps to hide the
+// shared-memory atomic latency with.
+template <typename T, int A_CT, int MODE, int NT>
+__global__ void __launch_bounds__(NT, 1) k_bin_private(BinArgs args, int64_t head, int64_t groups) {
     extern __shared__ __align__(16) unsigned char smem[];
     using V = typename VecOf<T>::type;
     constexpr int VN = VecOf<T>::N;
@@ -56,7 +60,8 @@ __global__ void __launch_bounds__(512) k_bin_private(BinArgs args, int64_t head,
     for (int64_t i = tid; i < head; i += nthreads) one(i);
     for (int64_t i = tail0 + tid; i < n; i += nthreads) one(i);
 
-    // vector body: groups of VN particles, two groups per thread per step
+    // vector body: groups of VN particles, U groups per thread per step
+    constexpr int U = NT >= 1024 ? 1 : 2;
     const V* __restrict__ XV = reinterpret_cast<const V*>(X + head);
     const V* __restrict__ YV = reinterpret_cast<const V*>(Y + head);
     if (A_CT >= 0) {
@@ -65,14 +70,14 @@ __global__ void __launch_bounds__(512) k_bin_private(BinArgs args, int64_t head,
 #pragma unroll
         for (int a = 0; a < AC; ++a)
             AV[a] = reinterpret_cast<const V*>(static_cast<const T*>(args.a[a < A ? a : 0]) + head);
-        // software pipeline: the loads of the next two groups are in flight
-        // while the current two are binned
+        // software pipeline: the loads of the next U groups are in flight
+        // while the current U are binned
         struct Stage {
-            V x[2], y[2], a[2][AC];
+            V x[U], y[U], a[U][AC];
         };
         auto load = [&](Stage& st, int64_t g) {
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const int64_t gg = g + u * nthreads;
                 if (gg < groups) {
                     st.x[u] = __ldcs(XV + gg);
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(512) k_bin_private(BinArgs args, int64_t head,
         };
         auto consume = [&](const Stage& st, int64_t g) {
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < U; ++u) {
                 if (g + u * nthreads >= groups) break;
 #pragma unroll
                 for (int j = 0; j < VN; ++j) {
@@ -100,8 +105,8 @@ __global__ void __launch_bounds__(512) k_bin_private(BinArgs args, int64_t head,
         Stage cur, nxt;
         int64_t gi = tid;
         if (gi < groups) load(cur, gi);
-        for (; gi < groups; gi += 2 * nthreads) {
-            const int64_t gn = gi + 2 * nthreads;
+        for (; gi < groups; gi += U * nthreads) {
+            const int64_t gn = gi + U * nthreads;
             if (gn < groups) load(nxt, gn);
             consume(cur, gi);
             cur = nxt;
@@ -166,9 +171,9 @@ size_t private_smem_bytes(const BinArgs& a, int smem_optin) {
     return b <= (size_t)smem_optin ? b : 0;
 }
 
-template <typename T, int A_CT, int MODE>
-static cudaError_t launch_private_t(const KernelCtx& kc, const BinArgs& a, size_t smem) {
-    auto kern = k_bin_private<T, A_CT, MODE>;
+template <typename T, int A_CT, int MODE, int NT>
+static cudaError_t configure_private(const KernelCtx& kc, size_t smem, int* per_sm) {
+    auto kern = k_bin_private<T, A_CT, MODE, NT>;
     static bool configured = false;  // per instantiation
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -176,11 +181,27 @@ static cudaError_t launch_private_t(const KernelCtx& kc, const BinArgs& a, size_
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int block = 512;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, NT, smem);
+}
+
+template <typename T, int A_CT, int MODE>
+static cudaError_t launch_private_t(const KernelCtx& kc, const BinArgs& a, size_t smem) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+    cudaError_t e = configure_private<T, A_CT, MODE, 512>(kc, smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // one 512-thread CTA per SM leaves it at 16 warps: use 1024 threads
+    // (the generic any-attribute instance keeps 512)
+    bool wide = false;
+    if constexpr (A_CT >= 0) {
+        if (per_sm == 1) {
+            int per_sm_w = 0;
+            e = configure_private<T, A_CT, MODE, 1024>(kc, smem, &per_sm_w);
+            if (e != cudaSuccess) return e;
+            wide = per_sm_w >= 1;
+        }
+    }
+    const int block = wide ? 1024 : 512;
     int64_t head, groups;
     vector_split<T>(a, &head, &groups);
     // enough particles per CTA to amortise clearing and merging its mesh
@@ -189,7 +210,11 @@ static cudaError_t launch_private_t(const KernelCtx& kc, const BinArgs& a, size_
     if (want < 1) want = 1;
     int64_t grid = (int64_t)kc.num_sms * per_sm;
     if (grid > want) grid = want;
-    kern<<<(int)grid, block, smem, kc.stream>>>(a, head, groups);
+    if constexpr (A_CT >= 0) {
+        if (wide)
+            k_bin_private<T, A_CT, MODE, 1024><<<(int)grid, block, smem, kc.stream>>>(a, head, groups);
+    }
+    if (!wide) k_bin_private<T, A_CT, MODE, 512><<<(int)grid, block, smem, kc.stream>>>(a, head, groups);
     kc.count_launch();
     return cudaGetLastError();
 }
