@@ -60,8 +60,11 @@ template <> struct GBinner<double> {
     }
 };
 
-template <typename T, int A_CT>
-__global__ void __launch_bounds__(256) k_bin_global(BinArgs args, int64_t head, int64_t groups) {
+// NT threads per CTA: 256 without a window; with a shared-memory window one
+// CTA fills an SM's shared memory, so it runs 1024 threads (at most 64
+// registers) to keep 32 warps per SM.
+template <typename T, int A_CT, int NT>
+__global__ void __launch_bounds__(NT) k_bin_global(BinArgs args, int64_t head, int64_t groups) {
     extern __shared__ __align__(16) unsigned char wsmem[];
     using V = typename GVec<T>::type;
     constexpr int VN = GVec<T>::N;
@@ -193,31 +196,37 @@ template <typename T, int A_CT>
 static cudaError_t launch_global_t(const KernelCtx& kc, const BinArgs& a) {
     int64_t head, groups;
     gvector_split<T>(a, &head, &groups);
-    const int block = 256;
-    int64_t work = groups > 0 ? groups : a.n;
-    int64_t grid = (work + block - 1) / block;
-    int64_t cap = (int64_t)kc.num_sms * 8;
-    size_t smem = 0;
-    auto kern = k_bin_global<T, A_CT>;
-    if (a.win_nx > 0) {
-        // one window copy per CTA: as many CTAs as fit, all resident
-        smem = global_window_bytes(a.win_nx * a.win_ny, a.n_attrs, a.st.do_sum != 0);
-        static bool configured = false;
-        if (!configured) {
-            cudaFuncAttributes fa;
-            cudaError_t e = cudaFuncGetAttributes(&fa, kern);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kc.smem_optin - (int)fa.sharedSizeBytes);
-            if (e != cudaSuccess) return e;
-            configured = true;
-        }
-        int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        cap = (int64_t)kc.num_sms * per_sm;
+    const int64_t work = groups > 0 ? groups : a.n;
+    if (a.win_nx <= 0) {
+        const int block = 256;
+        int64_t grid = (work + block - 1) / block;
+        const int64_t cap = (int64_t)kc.num_sms * 8;
+        if (grid > cap) grid = cap;
+        if (grid < 1) grid = 1;
+        k_bin_global<T, A_CT, 256><<<(int)grid, block, 0, kc.stream>>>(a, head, groups);
+        kc.count_launch();
+        return cudaGetLastError();
     }
+    // one window copy per CTA: as many 1024-thread CTAs as fit, all resident
+    const int block = 1024;
+    auto kern = k_bin_global<T, A_CT, 1024>;
+    const size_t smem = global_window_bytes(a.win_nx * a.win_ny, a.n_attrs, a.st.do_sum != 0);
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kc.smem_optin - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int64_t grid = (work + block - 1) / block;
+    const int64_t cap = (int64_t)kc.num_sms * per_sm;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     kern<<<(int)grid, block, smem, kc.stream>>>(a, head, groups);
