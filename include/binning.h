@@ -386,6 +386,9 @@ typedef struct bn_server_stats {
  * while their memory fits `budget_bytes`, and merges admitted requests into
  * batched launches that overlap on the device with other work (continuous
  * batching). Each request's result is identical to binning its block alone.
+ * Server batches never run the autotuner's timed trials (they synchronise
+ * with the device and would stall every queued request): a shape class the
+ * context has tuned keeps its measured choice, others take the heuristic one.
  */
 BN_API bn_status bn_server_create(bn_context* ctx, const bn_server_options* opt, bn_server** srv);
 

@@ -94,6 +94,10 @@ struct Plan {
     cudaError_t err = cudaSuccess;
     size_t h2d_bytes = 0, d2h_bytes = 0;
     int strategy = 0;
+    // false: an unseen shape class takes the heuristic strategy instead of
+    // timing the candidates (the trials synchronise with the device; a
+    // latency-bound caller such as the server must not wait on them)
+    bool may_tune = true;
 
     explicit Plan(bn_context* c) : ctx(c), stream(c->stream) {}
     Plan(bn_context* c, cudaStream_t s) : ctx(c), stream(s) {}

@@ -533,9 +533,6 @@ int bn::choose_strategy(const BinArgs& a, int smem_optin, int num_sms, uint32_t 
     // Privatise when the mesh fits and there are enough particles per CTA
     // copy of the mesh to amortise clearing and merging it.
     if (smem > 0 && a.n >= 2 * B) return BN_STRATEGY_PRIVATE;
-    // Bucketed sort + reduce when the per-tile bucket table stays small next
-    // to the records (few buckets per tile) and there is enough work to
-    // stream; otherwise atomics straight into the global mesh.
     // Bucketed sort + reduce when the mesh state is larger than L2 (so
     // global atomics would go to DRAM), the per-tile bucket table stays
     // small next to the records, and there is enough work to stream.
@@ -681,7 +678,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
                     args.win_nx = it->second.win_nx;
                     args.win_ny = it->second.win_ny;
                 }
-            } else if (n >= (int64_t)1 << 16 && !accumulate) {
+            } else if (n >= (int64_t)1 << 16 && !accumulate && plan.may_tune) {
                 trial = true;
             }
         }

@@ -113,6 +113,7 @@ static void launch_batch(bn_server* s, Slot& slot, std::vector<Job*>& batch) {
     bn_context* c = s->ctx;
     std::lock_guard<std::mutex> lk(c->enqueue_mu);
     Plan plan(c, slot.stream);
+    plan.may_tune = false;  // shape classes the context has tuned keep their choice
     for (Job* j : batch) {
         if (j->copied) cudaStreamWaitEvent(slot.stream, j->copied, 0);
         bn_status st = enqueue_bin(c, plan, &j->block.x, &j->block.y, j->block.attrs,

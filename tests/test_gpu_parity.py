@@ -498,6 +498,29 @@ def test_server_results_equal_alone(bn, ctx):
         check(w, g, TOL_F32C)
 
 
+def test_server_does_not_run_autotuner_trials(bn):
+    """Server batches take tuned or heuristic strategies, never timed trials."""
+    import paper_2310_02926_gb300 as pkg
+    fresh = pkg.Context(0)
+    w = workloads.uniform(n=1 << 17, seed=21, res=48)
+    cols = [torch.from_numpy(c).cuda() for c in (w.x, w.y, *w.attrs)]
+    srv = bn.bn_server_create(fresh.handle, 1 << 28, max_inflight=2, max_batch=4)
+    o = bn.alloc_outputs(len(w.attrs), 48 * 48, torch.float64, torch.device("cuda"))
+    r = bn.result_struct(o)
+    blk = bn.block(cols[0], cols[1], cols[2:], bn.grid(w.lo, w.hi, w.res), r)
+    req = bn.bn_server_submit(srv, blk, bn.OP_ALL)
+    assert bn.bn_wait(req, 60_000_000) == bn.OK
+    bn.bn_request_release(req)
+    bn.bn_server_destroy(srv)
+    assert bn.bn_context_autotune_report(fresh.handle) == ""
+    check(w, to_numpy_result(o), TOL_F64)
+    # a direct call of the same shape class does tune
+    fresh.bin_particles(cols[0], cols[1], cols[2:], w.lo, w.hi, w.res)
+    torch.cuda.synchronize()
+    assert "attrs=2" in bn.bn_context_autotune_report(fresh.handle)
+    fresh.close()
+
+
 @pytest.mark.parametrize("inputs", ["host", "device_tight_budget", "strided"])
 def test_server_staging_paths(bn, ctx, inputs):
     """Requests whose columns are on the host, or that arrive while the budget
