@@ -57,24 +57,25 @@ struct BinArgs {
 
 // Plan of the bucketed sort + reduce (k_sort.cu). Sizes are set by
 // sort_plan; the device pointers by launch_bin_sort from one scratch block.
+// Record positions are 32-bit: the plan requires n < 2^31 - 2^16.
 struct SortDesc {
     int log2bk;        // bins per bucket = 1 << log2bk
     int nb;            // buckets
     int tp;            // particles per pass-1 tile
     int per;           // particles per pass-1 thread (tp / per threads)
-    int chunk;         // records per pass-2 work item (about)
+    int chunk;         // records per pass-2 work item (at most)
+    int pad0;
     int64_t tiles;     // pass-1 tiles
-    int64_t slots;     // tiles * tp record slots
+    int64_t slots;     // record slots (= n; attribute column stride)
     int64_t max_items;
-    int off_skey, off_sattr, off_mesh, pad;
-    size_t smem_scatter, smem_reduce;
-    unsigned short* keys;  // [slots] bin within bucket
-    void* attrs;           // [n_attrs][slots] attribute values
-    int* table;            // [tiles][nb + 1] bucket offsets within each tile
-    int* table_t;          // [nb + 1][tiles] the same, transposed
-    int* bucket_total;     // [nb]
-    int4* items;           // [max_items] {bucket, tile0, tile1, sole}
-    int* counters;         // [0] items, [1] next item to take
+    int off_gpos, off_skey, off_sbk, off_sattr;  // pass-1 shared-memory layout
+    size_t smem_count, smem_scatter, smem_reduce;
+    unsigned short* keys;    // [slots] bin within the bucket, bucket-contiguous
+    void* attrs;             // [n_attrs][slots] attribute values, same order
+    unsigned* bucket_total;  // [nb] records per bucket
+    unsigned* cursor;        // [nb] next free record slot of each bucket
+    int4* items;             // [max_items] {bucket, first record, end record, sole}
+    int* counters;           // [0] items, [1] next item to take
 };
 
 bool sort_plan(const BinArgs& a, int smem_optin, SortDesc* sd);

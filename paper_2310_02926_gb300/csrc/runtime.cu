@@ -534,13 +534,13 @@ int bn::choose_strategy(const BinArgs& a, int smem_optin, int num_sms, uint32_t 
     // copy of the mesh to amortise clearing and merging it.
     if (smem > 0 && a.n >= 2 * B) return BN_STRATEGY_PRIVATE;
     // Bucketed sort + reduce when the mesh state is larger than L2 (so
-    // global atomics would go to DRAM), the per-tile bucket table stays
-    // small next to the records, and there is enough work to stream.
+    // global atomics would go to DRAM), a pass-1 tile feeds few enough
+    // buckets (run reservations at most one per four records), and there is
+    // enough work to stream.
     const size_t tsz = a.dtype == BN_F64 ? 8 : 4;
     const double state = (double)B * (8 + a.n_attrs * (8 + 2 * tsz));
-    const double rec = 2.0 + a.n_attrs * (double)tsz;
     SortDesc sd;
-    if (state > 128e6 && sort_plan(a, smem_optin, &sd) && (sd.nb + 1) * 4.0 <= 0.5 * rec * sd.tp &&
+    if (state > 128e6 && sort_plan(a, smem_optin, &sd) && 4 * sd.nb <= sd.tp &&
         a.n >= (int64_t)num_sms * sd.tp && a.n >= B / 4)
         return BN_STRATEGY_SORT;
     return BN_STRATEGY_GLOBAL;
