@@ -212,7 +212,7 @@ struct SmemMesh {
                     if (do_mm) {
                         const K2 cur = mm[k];
                         if (st.mmk) {
-                            static_cast<K2*>(st.mmk)[(int64_t)a * st.bins + b] = cur;
+                            static_cast<K2*>(st.mmk)[b * key_record_pairs(st.n_attrs, (int)sizeof(K)) + a] = cur;
                         } else {
                             if (do_min) static_cast<T*>(st.mn[a])[b] = KO::value(cur.x);
                             if (do_max) static_cast<T*>(st.mx[a])[b] = KO::value(cur.y);
@@ -228,7 +228,7 @@ struct SmemMesh {
                 if (do_sum) atomicAdd(&st.sum[a][b], sum_value(k));
                 if (do_mm && st.mmk) {
                     const K2 cur = mm[k];
-                    K2* kp = static_cast<K2*>(st.mmk) + (int64_t)a * st.bins + b;
+                    K2* kp = static_cast<K2*>(st.mmk) + b * key_record_pairs(st.n_attrs, (int)sizeof(K)) + a;
                     const K2 g = __ldca(kp);
                     if (do_min && cur.x < g.x) atomicMin(&kp->x, cur.x);
                     if (do_max && cur.y > g.y) atomicMax(&kp->y, cur.y);
@@ -256,6 +256,32 @@ struct SmemMesh {
 // never above the true max, so a stale read only admits extra atomics.
 template <typename T>
 __device__ __forceinline__ T filter_load(const T* p) { return __ldca(p); }
+
+// The first np pairs (a multiple of the pairs in 32 bytes) of bin b's key
+// record (StateDesc::mmk), read with 256-bit loads: one L2 request per two
+// f64 (four f32) attributes. Cached in L1 like filter_load: a stale record
+// only lets through an atomic that turns out to be unnecessary.
+__device__ __forceinline__ void load_key_record(const longlong2* rec, longlong2* out, int np) {
+    for (int c = 0; c < np; c += 2) {
+        unsigned long long w0, w1, w2, w3;
+        asm("ld.global.ca.v4.u64 {%0, %1, %2, %3}, [%4];"
+            : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
+            : "l"(rec + c));
+        out[c] = make_longlong2((long long)w0, (long long)w1);
+        out[c + 1] = make_longlong2((long long)w2, (long long)w3);
+    }
+}
+__device__ __forceinline__ void load_key_record(const int2* rec, int2* out, int np) {
+    for (int c = 0; c < np; c += 4) {
+        unsigned long long w[4];
+        asm("ld.global.ca.v4.u64 {%0, %1, %2, %3}, [%4];"
+            : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3])
+            : "l"(rec + c));
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            out[c + j] = make_int2((int)(unsigned)(w[j] & 0xffffffffu), (int)(unsigned)(w[j] >> 32));
+    }
+}
 
 // Combine the lanes of the calling warp that share bin b (b >= 0) and let
 // the lowest such lane update the global mesh. Every lane of the warp must
@@ -288,6 +314,18 @@ __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, c
         const int ws = win ? win->slot(b) : -1;
         if (ws >= 0) atomicAdd(&win->cnt[ws], 1u);
         else atomicAdd(&st.count[b], 1ull);
+        using KO = KeyOf<T>;
+        using K2 = typename KO::K2;
+        constexpr int RPC = A_CT > 0 ? (A_CT + 32 / (int)sizeof(K2) - 1) / (32 / (int)sizeof(K2)) * (32 / (int)sizeof(K2))
+                                     : kMaxAttr;
+        K2 rec[RPC];
+        K2* kr = nullptr;
+        if (st.mmk && (st.do_min || st.do_max)) {
+            // the bin's whole key record, 32 bytes per load
+            const int rp = key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
+            kr = static_cast<K2*>(st.mmk) + (int64_t)b * rp;
+            load_key_record(kr, rec, key_record_pairs(A, (int)sizeof(typename KO::K)));
+        }
         for (int a = 0; a < A; ++a) {
             const T x = v[a];
             if (st.do_sum) {
@@ -295,14 +333,10 @@ __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, c
                 else atomicAdd(&st.sum[a][b], (double)x);
             }
             if (is_nan_bits(x)) continue;
-            if (st.mmk) {
-                // one 16-byte (f64) or 8-byte (f32) read for both keys
-                using KO = KeyOf<T>;
-                auto* kp = static_cast<typename KO::K2*>(st.mmk) + (int64_t)a * st.bins + b;
+            if (kr) {
                 const auto key = KO::key(x);
-                const auto cur = __ldca(kp);
-                if (st.do_min && key < cur.x) atomicMin(&kp->x, key);
-                if (st.do_max && key > cur.y) atomicMax(&kp->y, key);
+                if (st.do_min && key < rec[a].x) atomicMin(&kr[a].x, key);
+                if (st.do_max && key > rec[a].y) atomicMax(&kr[a].y, key);
                 continue;
             }
             if (st.do_min) {
@@ -350,18 +384,26 @@ __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, c
     const int ws = win ? win->slot(b) : -1;
     if (ws >= 0) atomicAdd(&win->cnt[ws], cnt);
     else atomicAdd(&st.count[b], (unsigned long long)cnt);
+    using KO = KeyOf<T>;
+    using K2 = typename KO::K2;
+    constexpr int RPC = A_CT > 0 ? (A_CT + 32 / (int)sizeof(K2) - 1) / (32 / (int)sizeof(K2)) * (32 / (int)sizeof(K2))
+                                 : kMaxAttr;
+    K2 rec[RPC];
+    K2* kr = nullptr;
+    if (st.mmk && (st.do_min || st.do_max)) {
+        const int rp = key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
+        kr = static_cast<K2*>(st.mmk) + (int64_t)b * rp;
+        load_key_record(kr, rec, key_record_pairs(A, (int)sizeof(typename KO::K)));
+    }
     for (int a = 0; a < A; ++a) {
         if (st.do_sum) {
             if (ws >= 0) atomicAdd(&win->sum[a * win->W + ws], s[a]);
             else atomicAdd(&st.sum[a][b], s[a]);
         }
-        if (st.mmk) {
-            using KO = KeyOf<T>;
-            auto* kp = static_cast<typename KO::K2*>(st.mmk) + (int64_t)a * st.bins + b;
-            const auto cur = __ldca(kp);
+        if (kr) {
             const auto kl = KO::key(lo[a]), kh = KO::key(hi[a]);
-            if (st.do_min && kl < cur.x) atomicMin(&kp->x, kl);
-            if (st.do_max && kh > cur.y) atomicMax(&kp->y, kh);
+            if (st.do_min && kl < rec[a].x) atomicMin(&kr[a].x, kl);
+            if (st.do_max && kh > rec[a].y) atomicMax(&kr[a].y, kh);
             continue;
         }
         if (st.do_min && !(lo[a] == pos_inf<T>())) {

@@ -59,10 +59,13 @@ struct StateDesc {
     void* mn[kMaxAttr];
     void* mx[kMaxAttr];
     double* avg[kMaxAttr];
-    // Optional min/max state as interleaved totalOrder keys, [n_attrs][bins]
-    // pairs {min key, max key} (long long for f64, int for f32). When set,
-    // the particle pass updates these instead of mn/mx and k_finalize writes
-    // mn/mx from them; when null, mn/mx hold the running min/max directly.
+    // Optional min/max state as totalOrder keys: per bin one record of
+    // key_record_pairs(n_attrs, sizeof T) pairs {min key, max key} (long long
+    // for f64, int for f32), attribute a at pair a, padded to whole 32-byte
+    // pieces so that one 256-bit load reads the pairs of two f64 (four f32)
+    // attributes. When set, the particle pass updates these instead of mn/mx
+    // and k_finalize writes mn/mx from them; when null, mn/mx hold the
+    // running min/max directly.
     void* mmk;
     int64_t bins;
     int32_t n_attrs;
@@ -72,6 +75,13 @@ struct StateDesc {
     int32_t do_avg;
     int32_t pad;
 };
+
+// Key pairs per bin record of StateDesc::mmk: n_attrs rounded up to the pairs
+// of one 32-byte piece (2 for 8-byte keys, 4 for 4-byte keys).
+__host__ __device__ __forceinline__ int key_record_pairs(int n_attrs, int key_bytes) {
+    const int q = 32 / (2 * key_bytes);
+    return (n_attrs + q - 1) / q * q;
+}
 
 // ---------------------------------------------------------------- bits
 __device__ __forceinline__ bool is_nan_bits(float v) {

@@ -64,7 +64,7 @@ struct SortDesc {
     int tp;            // particles per pass-1 tile
     int per;           // particles per pass-1 thread (tp / per threads)
     int chunk;         // records per pass-2 work item (at most)
-    int pad0;
+    int accumulate;    // 1: items merge into the existing state (never store a whole bucket)
     int64_t tiles;     // pass-1 tiles
     int64_t slots;     // record slots (= n; attribute column stride)
     int64_t max_items;

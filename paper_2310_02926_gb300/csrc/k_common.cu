@@ -27,18 +27,19 @@ __global__ void k_init_state(StateDesc st, T* bounds_acc) {
         bounds_acc[3] = neg_inf<T>();
     }
     for (int64_t b = t0; b < B; b += stride) st.count[b] = 0ull;
+    if (st.mmk) {
+        using KO = KeyOf<T>;
+        typename KO::K2 init;
+        init.x = KO::kPosInf;
+        init.y = KO::kNegInf;
+        const int64_t pairs = B * key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
+        auto* kp = static_cast<typename KO::K2*>(st.mmk);
+        for (int64_t q = t0; q < pairs; q += stride) kp[q] = init;
+    }
     for (int a = 0; a < st.n_attrs; ++a) {
         if (st.do_sum)
             for (int64_t b = t0; b < B; b += stride) st.sum[a][b] = 0.0;
-        if (st.mmk) {
-            using KO = KeyOf<T>;
-            typename KO::K2 init;
-            init.x = KO::kPosInf;
-            init.y = KO::kNegInf;
-            auto* kp = static_cast<typename KO::K2*>(st.mmk) + (int64_t)a * B;
-            for (int64_t b = t0; b < B; b += stride) kp[b] = init;
-            continue;
-        }
+        if (st.mmk) continue;
         if (st.do_min) {
             T* p = static_cast<T*>(st.mn[a]);
             for (int64_t b = t0; b < B; b += stride) p[b] = pos_inf<T>();
@@ -209,7 +210,8 @@ __global__ void k_finalize(StateDesc st) {
         for (int a = 0; a < st.n_attrs; ++a) {
             if (st.do_avg) st.avg[a][b] = c ? __ddiv_rn(st.sum[a][b], dc) : qnan;
             if (st.mmk) {
-                const auto k = static_cast<const typename KO::K2*>(st.mmk)[(int64_t)a * B + b];
+                const int rp = key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
+                const auto k = static_cast<const typename KO::K2*>(st.mmk)[b * rp + a];
                 if (st.do_min) static_cast<T*>(st.mn[a])[b] = KO::value(k.x);
                 if (st.do_max) static_cast<T*>(st.mx[a])[b] = KO::value(k.y);
             }

@@ -109,7 +109,9 @@ __global__ void __launch_bounds__(512) k_sort_count(BinArgs args, SortDesc sd) {
 
 // ------------------------------------------------------------------ plan
 // One block: bucket totals -> first record slot of each bucket (into the
-// cursors) and work items {bucket, first record, end record, sole}.
+// cursors) and work items {bucket, first record, end record, sole}. A sole
+// item (the only one of its bucket) stores the bucket's bins outright,
+// except when accumulating into existing outputs.
 __global__ void k_sort_plan(SortDesc sd) {
     __shared__ int warp_sums[32];
     __shared__ int s_total;
@@ -133,7 +135,7 @@ __global__ void k_sort_plan(SortDesc sd) {
             it.x = k;
             it.y = rec_off + (int)((int64_t)j * c / parts);
             it.z = rec_off + (int)((int64_t)(j + 1) * c / parts);
-            it.w = parts == 1 ? 1 : 0;
+            it.w = (parts == 1 && !sd.accumulate) ? 1 : 0;
             sd.items[off + j] = it;
         }
         off += parts;

@@ -685,6 +685,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         if (strat == BN_STRATEGY_PRIVATE && private_smem_bytes(args, c->smem_optin) == 0)
             return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_PRIVATE: the mesh does not fit in shared memory");
         const bool sort_ok = sort_plan(args, c->smem_optin, &sortd);
+        sortd.accumulate = accumulate ? 1 : 0;
         if (strat == BN_STRATEGY_SORT && !sort_ok)
             return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_SORT: the mesh has too many buckets for the sort path");
         if (strat == BN_STRATEGY_SORT || (trial && sort_ok)) {
@@ -692,7 +693,8 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
             if (!sort_scratch) return cuda_fail(plan.err, "cudaMallocAsync(sort scratch)");
         }
         if ((strat == BN_STRATEGY_GLOBAL || trial) && !accumulate && n_attrs > 0 && (want_min || want_max)) {
-            sd.mmk = plan.alloc((size_t)n_attrs * B * 2 * dtype_size(dtype));
+            sd.mmk = plan.alloc((size_t)key_record_pairs(n_attrs, (int)dtype_size(dtype)) * B * 2 *
+                                dtype_size(dtype));
             if (!sd.mmk) return cuda_fail(plan.err, "cudaMallocAsync(min/max keys)");
         }
     }

@@ -308,13 +308,17 @@ def test_library_allocated_outputs(bn, ctx):
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-def test_accumulate_shards_into_one_state(bn, ctx, dtype):
-    w = workloads.plummer(400_000, seed=13, dtype=dtype, res=128)
+@pytest.mark.parametrize("strategy", ["auto", "private", "global", "sort"])
+def test_accumulate_shards_into_one_state(bn, ctx, dtype, strategy):
+    """Shards binned one after another into the same outputs (BN_OP_ACCUMULATE)
+    equal the whole set binned at once, whatever strategy each shard takes."""
+    res = 32 if strategy == "private" else 128  # the private mesh must fit shared memory
+    w = workloads.plummer(400_000, seed=13, dtype=dtype, res=res)
     cols = [torch.from_numpy(c).cuda() for c in (w.x, w.y, *w.attrs)]
-    out = bn.alloc_outputs(3, 128 * 128, cols[0].dtype, torch.device("cuda"))
+    out = bn.alloc_outputs(3, res * res, cols[0].dtype, torch.device("cuda"))
     cuts = [0, 1, 150_000, 150_003, w.n]
     for k, (a, b) in enumerate(zip(cuts[:-1], cuts[1:])):
-        ops = bn.OP_ALL | (bn.OP_ACCUMULATE if k else 0)
+        ops = bn.OP_ALL | (bn.OP_ACCUMULATE if k else 0) | sflag(bn, strategy)
         ctx.bin_particles(cols[0][a:b], cols[1][a:b], [c[a:b] for c in cols[2:]], w.lo, w.hi,
                           w.res, ops=ops, out=out)
     torch.cuda.synchronize()
