@@ -262,6 +262,10 @@ __device__ __forceinline__ T filter_load(const T* p) { return __ldca(p); }
 // f64 (four f32) attributes. Cached in L1 like filter_load: a stale record
 // only lets through an atomic that turns out to be unnecessary.
 __device__ __forceinline__ void load_key_record(const longlong2* rec, longlong2* out, int np) {
+    if (np == 1) {  // a 16-byte record
+        out[0] = __ldca(rec);
+        return;
+    }
     for (int c = 0; c < np; c += 2) {
         unsigned long long w0, w1, w2, w3;
         asm("ld.global.ca.v4.u64 {%0, %1, %2, %3}, [%4];"
@@ -272,6 +276,12 @@ __device__ __forceinline__ void load_key_record(const longlong2* rec, longlong2*
     }
 }
 __device__ __forceinline__ void load_key_record(const int2* rec, int2* out, int np) {
+    if (np == 2) {  // a 16-byte record
+        const int4 v = __ldca(reinterpret_cast<const int4*>(rec));
+        out[0] = make_int2(v.x, v.y);
+        out[1] = make_int2(v.z, v.w);
+        return;
+    }
     for (int c = 0; c < np; c += 4) {
         unsigned long long w[4];
         asm("ld.global.ca.v4.u64 {%0, %1, %2, %3}, [%4];"

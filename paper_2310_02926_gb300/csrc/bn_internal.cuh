@@ -61,9 +61,9 @@ struct StateDesc {
     double* avg[kMaxAttr];
     // Optional min/max state as totalOrder keys: per bin one record of
     // key_record_pairs(n_attrs, sizeof T) pairs {min key, max key} (long long
-    // for f64, int for f32), attribute a at pair a, padded to whole 32-byte
-    // pieces so that one 256-bit load reads the pairs of two f64 (four f32)
-    // attributes. When set, the particle pass updates these instead of mn/mx
+    // for f64, int for f32), attribute a at pair a, padded to 16 bytes or to
+    // whole 32-byte pieces so that one 256-bit load reads the pairs of two
+    // f64 (four f32) attributes. When set, the particle pass updates these instead of mn/mx
     // and k_finalize writes mn/mx from them; when null, mn/mx hold the
     // running min/max directly.
     void* mmk;
@@ -76,10 +76,13 @@ struct StateDesc {
     int32_t pad;
 };
 
-// Key pairs per bin record of StateDesc::mmk: n_attrs rounded up to the pairs
-// of one 32-byte piece (2 for 8-byte keys, 4 for 4-byte keys).
+// Key pairs per bin record of StateDesc::mmk: a record of at most 16 bytes is
+// padded to 16 (one 128-bit load), a longer one to whole 32-byte pieces
+// (256-bit loads: 2 pairs of 8-byte keys, 4 of 4-byte keys per piece).
 __host__ __device__ __forceinline__ int key_record_pairs(int n_attrs, int key_bytes) {
-    const int q = 32 / (2 * key_bytes);
+    const int pair = 2 * key_bytes;
+    if (n_attrs * pair <= 16) return 16 / pair;
+    const int q = 32 / pair;
     return (n_attrs + q - 1) / q * q;
 }
 

@@ -95,6 +95,24 @@ def test_autotuned_calls_repeat_exactly(bn, dtype):
         c.close()
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("n_attrs", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("aggregate", [False, True])
+def test_global_key_records_any_attribute_count(bn, ctx, dtype, n_attrs, aggregate):
+    """Global strategy: each bin's min/max keys form one record of all
+    attributes, padded to 32-byte pieces (read with 256-bit loads); every
+    attribute count, odd or past one piece, and both commit paths."""
+    rng = np.random.default_rng(60 + n_attrs)
+    n = 300_001
+    x = rng.normal(0.5, 0.15, n).astype(dtype)
+    y = rng.normal(0.5, 0.15, n).astype(dtype)
+    attrs = [rng.standard_normal(n).astype(dtype) * (k + 1) for k in range(n_attrs)]
+    attrs[0][::97] = np.nan
+    w = workloads.Workload("records", x, y, attrs, (0.0, 0.0), (1.0, 1.0), (300, 200))
+    flags = bn.STRATEGY_GLOBAL | (bn.AGG_ON if aggregate else bn.AGG_OFF)
+    check(w, run_gpu(ctx, w, flags=flags), TOL_F64 if dtype == np.float64 else TOL_F32C)
+
+
 def test_private_rejects_mesh_too_large_for_shared_memory(bn, ctx):
     w = workloads.plummer(10_000, seed=2, dtype=np.float64, res=1024)
     with pytest.raises(bn.BinningError) as e:
