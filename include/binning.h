@@ -25,9 +25,11 @@
  *  - A "device buffer" is memory that the context's device can read with
  *    ordinary loads: cudaMalloc/cudaMallocAsync/torch CUDA memory on that
  *    device. A buffer with device == BN_HOST is host memory (pageable or
- *    pinned); the library copies it to/from a device temporary (the
- *    location-agnostic access of Sec. 2, "PM Interoperability and Location
- *    Agnostic Access").
+ *    pinned), reached by the location-agnostic access of Sec. 2 ("PM
+ *    Interoperability and Location Agnostic Access"): a contiguous input
+ *    column in page-locked (pinned or registered) host memory is read in
+ *    place by the kernels over the host link; other host inputs, and host
+ *    outputs, go through a device temporary.
  *  - A buffer on a different CUDA device than the context's is rejected
  *    with BN_ERR_DEVICE_MISMATCH.
  *
@@ -270,8 +272,9 @@ BN_API bn_status bn_context_profile(bn_context* ctx, double* total_ms, uint64_t*
  * Bin n particles (Sec. 4.2) with coordinates x, y and n_attrs attribute
  * columns onto `grid`, producing the reductions selected in `ops`.
  *   x, y, attrs[0..n_attrs)  same n and dtype (BN_F32 or BN_F64); device
- *                            buffers are read in place (zero copy), host
- *                            buffers are staged to the device
+ *                            buffers and contiguous page-locked host
+ *                            buffers are read in place (zero copy), other
+ *                            host buffers are staged to the device
  *   n_attrs                  0..BN_MAX_ATTR (0: count only); when `ops`
  *                            selects no sum, avg, min or max the columns are
  *                            validated but neither staged nor read

@@ -434,7 +434,21 @@ bn_status Plan::column(const bn_buffer* b, int dtype, const void** out) {
         *out = t;
         return BN_OK;
     }
-    // host memory: the location-agnostic access of Sec. 2 (temporary + move)
+    // host memory: the location-agnostic access of Sec. 2. Page-locked host
+    // memory is mapped into the device's address space: the kernels read a
+    // contiguous page-locked column in place over the host link (each input
+    // is read once, coalesced), with no temporary and no separate copy.
+    // Other host memory is moved into a temporary.
+    if (stride == 1) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, b->ptr) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer) {
+            h2d_bytes += (size_t)n * es;
+            *out = pa.devicePointer;
+            return BN_OK;
+        }
+        cudaGetLastError();  // an unregistered pointer is not an error here
+    }
     void* t = alloc((size_t)n * es);
     if (!t) return cuda_fail(err, "cudaMallocAsync(host column)");
     cudaError_t e;

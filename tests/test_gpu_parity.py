@@ -292,6 +292,25 @@ def test_host_inputs_and_outputs(bn, ctx):
     check(w, to_numpy_result(out2), TOL_F64)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("strategy", ["auto", "private", "global", "sort"])
+@pytest.mark.parametrize("auto_bounds", [False, True])
+def test_pinned_host_columns_read_in_place(bn, ctx, dtype, strategy, auto_bounds):
+    """Page-locked host columns are read by the kernels over the host link;
+    slices start inside the pinned block at odd element offsets."""
+    w = workloads.plummer(400_003, seed=19, dtype=dtype, res=40)
+    off = 3
+    pinned = [torch.from_numpy(np.concatenate([np.zeros(off, c.dtype), c])).pin_memory()
+              for c in (w.x, w.y, *w.attrs)]
+    cols = [t[off:] for t in pinned]
+    out = bn.alloc_outputs(3, 40 * 40, cols[0].dtype, torch.device("cuda"))
+    ctx.bin_particles(cols[0], cols[1], cols[2:], w.lo, w.hi, w.res, auto_bounds,
+                      bn.OP_ALL | sflag(bn, strategy), out=out)
+    torch.cuda.synchronize()
+    check(w, to_numpy_result(out), TOL_F64 if dtype == np.float64 else TOL_F32C,
+          auto_bounds=auto_bounds)
+
+
 def test_library_allocated_outputs(bn, ctx):
     w = workloads.uniform(50_000, seed=12, dtype=np.float32, res=20)
     cols = [torch.from_numpy(c).cuda() for c in (w.x, w.y, *w.attrs)]
