@@ -294,7 +294,9 @@ def run_batch(args, n_blocks):
             o64 = bn.alloc_outputs(2, w.res[0] * w.res[1], torch.float64, dev)
             cols64.append((c64, bn.grid(w.lo, w.hi, w.res), bn.result_struct(o64), o64))
         gen_s = time.time() - t0
-        ops = bn.OP_ALL | bn.SUM_F32C
+        ops = bn.OP_ALL | bn.SUM_F32C | {"auto": 0, "global": bn.STRATEGY_GLOBAL,
+                                         "private": bn.STRATEGY_PRIVATE,
+                                         "sort": bn.STRATEGY_SORT}[args.strategy]
 
         def timed(fn, steps, warm):
             reqs = []

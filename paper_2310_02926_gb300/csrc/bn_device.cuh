@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include "bn_internal.cuh"
 
 namespace bn {
@@ -89,9 +91,20 @@ template <> struct KeyOf<double> {
 // otherwise. Min and max of one attribute and bin sit next to each other
 // as totalOrder keys, so one load reads both and the updates are plain
 // signed integer atomicMin / atomicMax.
+//
+// MODE kSumF64Keys (f64 only): the exact keys are the global key records
+// (StateDesc::mmk), and shared memory keeps per bin and attribute the top
+// 32 bits of the min and max keys as a filter ([B][A] int2). Every value the
+// filter holds belongs to a key already merged into the records, so a
+// particle the filter rejects cannot change them; one that passes updates
+// the record with a global atomic (an L2 reduction) and lowers (raises) the
+// filter. Half the shared-memory bytes per particle for min/max, and the
+// mesh leaves more room; data with many values tied at a bin's extreme pays
+// one L2 reduction per tied particle instead.
 template <typename T, int MODE>
 struct SmemMesh {
-    static constexpr bool kWide = sizeof(T) == 8 || MODE == kSumF64;
+    static constexpr bool kWide = sizeof(T) == 8 || MODE == kSumF64 || MODE == kSumF64Keys;
+    static constexpr bool kGK = MODE == kSumF64Keys;
     using KO = KeyOf<T>;
     using K = typename KO::K;
     using K2 = typename KO::K2;
@@ -100,8 +113,16 @@ struct SmemMesh {
     float* s32;
     float* c32;
     K2* mm;  // [A][B] {min key, max key}
+    int2* flt;  // kGK: [B][A] {top 32 bits of min key, of max key}
+    K2* gkeys;  // kGK: the global key records, gk_rp pairs per bin
+    int gk_rp, n_a;
     int B;
     bool do_sum, do_mm, do_min, do_max;
+
+    __device__ void bind_keys(const StateDesc& st) {
+        gkeys = static_cast<K2*>(st.mmk);
+        gk_rp = key_record_pairs(st.n_attrs, (int)sizeof(K));
+    }
 
     __device__ void carve(unsigned char* base, int B_, int A, bool s, bool lo, bool hi) {
         B = B_;
@@ -128,7 +149,11 @@ struct SmemMesh {
             }
         }
         off = (off + 15) & ~(size_t)15;
-        mm = do_mm ? reinterpret_cast<K2*>(base + off) : nullptr;
+        n_a = A;
+        mm = (do_mm && !kGK) ? reinterpret_cast<K2*>(base + off) : nullptr;
+        flt = (do_mm && kGK) ? reinterpret_cast<int2*>(base + off) : nullptr;
+        gkeys = nullptr;
+        gk_rp = 0;
     }
 
     __device__ void clear(int A) {
@@ -143,12 +168,14 @@ struct SmemMesh {
                     for (int k = threadIdx.x; k < AB; k += blockDim.x) c32[k] = 0.0f;
             }
         }
-        if (do_mm) {
+        if (do_mm && !kGK) {
             K2 init;
             init.x = KO::kPosInf;
             init.y = KO::kNegInf;
             for (int k = threadIdx.x; k < AB; k += blockDim.x) mm[k] = init;
         }
+        if (do_mm && kGK)
+            for (int k = threadIdx.x; k < AB; k += blockDim.x) flt[k] = make_int2(INT_MAX, INT_MIN);
     }
 
     __device__ __forceinline__ void add_count(int b) { atomicAdd(&cnt[b], 1u); }
@@ -174,12 +201,28 @@ struct SmemMesh {
                     atomicAdd(&c32[k], err);
             }
         }
-        if (do_mm) {
+        if (do_mm && !kGK) {
             if (is_nan_bits(v)) return;
             const K key = KO::key(v);
             const K2 cur = mm[k];
             if (do_min && key < cur.x) atomicMin(&mm[k].x, key);
             if (do_max && key > cur.y) atomicMax(&mm[k].y, key);
+        }
+        if (do_mm && kGK) {
+            if (is_nan_bits(v)) return;
+            const K key = KO::key(v);
+            const int h = (int)((long long)key >> 32);  // order preserving
+            int2* fp = flt + b * n_a + a;
+            const int2 f = *fp;
+            K2* kr = gkeys + (int64_t)b * gk_rp + a;
+            if (do_min && h <= f.x) {
+                atomicMin(&kr->x, key);
+                if (h < f.x) atomicMin(&fp->x, h);
+            }
+            if (do_max && h >= f.y) {
+                atomicMax(&kr->y, key);
+                if (h > f.y) atomicMax(&fp->y, h);
+            }
         }
     }
 
@@ -209,7 +252,7 @@ struct SmemMesh {
                 for (int a = 0; a < A; ++a) {
                     const int k = a * B + l;
                     if (do_sum) st.sum[a][b] = sum_value(k);
-                    if (do_mm) {
+                    if (do_mm && !kGK) {
                         const K2 cur = mm[k];
                         if (st.mmk) {
                             static_cast<K2*>(st.mmk)[b * key_record_pairs(st.n_attrs, (int)sizeof(K)) + a] = cur;
@@ -226,6 +269,7 @@ struct SmemMesh {
             for (int a = 0; a < A; ++a) {
                 const int k = a * B + l;
                 if (do_sum) atomicAdd(&st.sum[a][b], sum_value(k));
+                if (kGK) continue;  // min/max already in the global key records
                 if (do_mm && st.mmk) {
                     const K2 cur = mm[k];
                     K2* kp = static_cast<K2*>(st.mmk) + b * key_record_pairs(st.n_attrs, (int)sizeof(K)) + a;

@@ -13,7 +13,10 @@ namespace bn {
 constexpr int kMaxAttr = BN_MAX_ATTR;
 
 // ---------------------------------------------------------------- sum modes
-enum SumMode : int { kSumF32C = 0, kSumF32 = 1, kSumF64 = 2 };
+// kSumF64Keys: FP64 sums; the exact min/max keys live in global key
+// records (StateDesc::mmk) behind a 32-bit filter in shared memory (private
+// strategy, f64 data).
+enum SumMode : int { kSumF32C = 0, kSumF32 = 1, kSumF64 = 2, kSumF64Keys = 3 };
 
 // ---------------------------------------------------------------- mesh axis
 // One axis of the mesh with bounds and scale already rounded to the

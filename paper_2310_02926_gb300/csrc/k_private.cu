@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(NT, 1) k_bin_private(BinArgs args, int64_t hea
 
     SmemMesh<T, MODE> m;
     m.carve(smem, B, A, st.do_sum != 0, st.do_min != 0, st.do_max != 0);
+    if constexpr (MODE == kSumF64Keys) m.bind_keys(st);
     m.clear(A);
     Binner<T> binner;
     binner.init(g);
@@ -149,13 +150,21 @@ static void vector_split(const BinArgs& a, int64_t* head, int64_t* groups) {
 }
 
 static size_t private_bytes_for(int dtype, int mode, int B, int A, bool s, bool lo, bool hi) {
-    const bool wide = dtype == BN_F64 || mode == kSumF64;
+    const bool wide = dtype == BN_F64 || mode == kSumF64 || mode == kSumF64Keys;
     const size_t tsz = dtype == BN_F64 ? 8 : 4;
     size_t b = ((size_t)B * 4 + 15) & ~(size_t)15;
     if (s) b += (size_t)A * B * (wide ? 8 : (mode == kSumF32C ? 8 : 4));
     b = (b + 15) & ~(size_t)15;
-    if (lo || hi) b += (size_t)A * B * 2 * tsz;  // {min key, max key}
+    // {min key, max key}, or their top 32 bits as a filter (kSumF64Keys)
+    if (lo || hi) b += (size_t)A * B * (mode == kSumF64Keys ? 8 : 2 * tsz);
     return b;
+}
+
+// The mesh mode a particle pass uses: f64 min/max go through the global key
+// records when the runtime provides them.
+static int private_mode(const BinArgs& a) {
+    if (a.dtype != BN_F64) return a.sum_mode;
+    return (a.st.mmk && (a.st.do_min || a.st.do_max)) ? kSumF64Keys : kSumF64;
 }
 
 size_t private_mesh_bytes(int dtype, int sum_mode, int64_t bins, int n_attrs, bool s, bool lo, bool hi) {
@@ -165,9 +174,8 @@ size_t private_mesh_bytes(int dtype, int sum_mode, int64_t bins, int n_attrs, bo
 size_t private_smem_bytes(const BinArgs& a, int smem_optin) {
     const int64_t B = (int64_t)a.grid.ax[0].res * a.grid.ax[1].res;
     if (B > (1 << 20)) return 0;
-    size_t b = private_bytes_for(a.dtype, a.dtype == BN_F64 ? kSumF64 : a.sum_mode, (int)B,
-                                 a.n_attrs, a.st.do_sum != 0, a.st.do_min != 0,
-                                 a.st.do_max != 0);
+    size_t b = private_bytes_for(a.dtype, private_mode(a), (int)B, a.n_attrs, a.st.do_sum != 0,
+                                 a.st.do_min != 0, a.st.do_max != 0);
     return b <= (size_t)smem_optin ? b : 0;
 }
 
@@ -234,7 +242,9 @@ static cudaError_t dispatch_a(const KernelCtx& kc, const BinArgs& a, size_t smem
 cudaError_t launch_bin_private(const KernelCtx& kc, const BinArgs& a) {
     size_t smem = private_smem_bytes(a, kc.smem_optin);
     if (smem == 0) return cudaErrorInvalidValue;
-    if (a.dtype == BN_F64) return dispatch_a<double, kSumF64>(kc, a, smem);
+    if (a.dtype == BN_F64)
+        return private_mode(a) == kSumF64Keys ? dispatch_a<double, kSumF64Keys>(kc, a, smem)
+                                              : dispatch_a<double, kSumF64>(kc, a, smem);
     switch (a.sum_mode) {
         case kSumF32: return dispatch_a<float, kSumF32>(kc, a, smem);
         case kSumF64: return dispatch_a<float, kSumF64>(kc, a, smem);

@@ -696,6 +696,15 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
                 trial = true;
             }
         }
+        // min/max as global key records: the global strategy's state, and
+        // for f64 the private strategy's exact keys (behind a shared filter)
+        const bool keys_private = dtype == BN_F64 && (strat == BN_STRATEGY_PRIVATE || trial);
+        if ((strat == BN_STRATEGY_GLOBAL || keys_private || trial) && !accumulate && n_attrs > 0 &&
+            (want_min || want_max)) {
+            sd.mmk = plan.alloc((size_t)key_record_pairs(n_attrs, (int)dtype_size(dtype)) * B * 2 *
+                                dtype_size(dtype));
+            if (!sd.mmk) return cuda_fail(plan.err, "cudaMallocAsync(min/max keys)");
+        }
         if (strat == BN_STRATEGY_PRIVATE && private_smem_bytes(args, c->smem_optin) == 0)
             return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_PRIVATE: the mesh does not fit in shared memory");
         const bool sort_ok = sort_plan(args, c->smem_optin, &sortd);
@@ -705,11 +714,6 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         if (strat == BN_STRATEGY_SORT || (trial && sort_ok)) {
             sort_scratch = plan.alloc(sort_scratch_bytes(sortd, args));
             if (!sort_scratch) return cuda_fail(plan.err, "cudaMallocAsync(sort scratch)");
-        }
-        if ((strat == BN_STRATEGY_GLOBAL || trial) && !accumulate && n_attrs > 0 && (want_min || want_max)) {
-            sd.mmk = plan.alloc((size_t)key_record_pairs(n_attrs, (int)dtype_size(dtype)) * B * 2 *
-                                dtype_size(dtype));
-            if (!sd.mmk) return cuda_fail(plan.err, "cudaMallocAsync(min/max keys)");
         }
     }
     args.st = sd;
@@ -761,7 +765,9 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
             for (const Cand& cd : cands) {
                 BinArgs ta = args;
                 ta.aggregate = aggbits == BN_AGG_ON ? 1 : aggbits == BN_AGG_OFF ? 0 : cd.agg;
-                if (cd.strat != BN_STRATEGY_GLOBAL) ta.st.mmk = nullptr;
+                // the key records serve the global strategy, and f64 private meshes
+                if (cd.strat == BN_STRATEGY_SORT || (cd.strat == BN_STRATEGY_PRIVATE && dtype != BN_F64))
+                    ta.st.mmk = nullptr;
                 auto pass = [&]() {
                     return cd.strat == BN_STRATEGY_PRIVATE ? launch_bin_private(kc, ta)
                            : cd.strat == BN_STRATEGY_SORT  ? launch_bin_sort(kc, ta, sortd, sort_scratch)
@@ -890,7 +896,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
                      win.strat == BN_STRATEGY_GLOBAL && win.agg ? "+agg" : "", wbest[2] ? "+window" : "");
             c->tune_log.push_back(std::string(head) + times + tail);
         }
-        if (strat != BN_STRATEGY_GLOBAL) sd.mmk = nullptr;
+        if (strat == BN_STRATEGY_SORT || (strat == BN_STRATEGY_PRIVATE && dtype != BN_F64)) sd.mmk = nullptr;
         e = launch_init_state(kc, dtype, sd, nullptr);
         if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     }

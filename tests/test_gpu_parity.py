@@ -113,6 +113,22 @@ def test_global_key_records_any_attribute_count(bn, ctx, dtype, n_attrs, aggrega
     check(w, run_gpu(ctx, w, flags=flags), TOL_F64 if dtype == np.float64 else TOL_F32C)
 
 
+@pytest.mark.parametrize("strategy", ["private", "global"])
+def test_min_max_with_tied_extremes(bn, ctx, strategy):
+    """Attributes whose values tie at a bin's extreme (a constant column, a
+    two-valued column, signed zeros): every tied particle reaches the exact
+    keys; results stay exact."""
+    rng = np.random.default_rng(71)
+    n = 500_000
+    x = rng.random(n)
+    y = rng.random(n)
+    const = np.full(n, 1.25)
+    two = np.where(rng.random(n) < 0.5, -3.0, 7.0)
+    zeros = np.where(rng.random(n) < 0.5, -0.0, 0.0)
+    w = workloads.Workload("ties", x, y, [const, two, zeros], (0.0, 0.0), (1.0, 1.0), (48, 40))
+    check(w, run_gpu(ctx, w, flags=sflag(bn, strategy)), TOL_F64)
+
+
 def test_private_rejects_mesh_too_large_for_shared_memory(bn, ctx):
     w = workloads.plummer(10_000, seed=2, dtype=np.float64, res=1024)
     with pytest.raises(bn.BinningError) as e:
