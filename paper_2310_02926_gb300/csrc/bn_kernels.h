@@ -107,7 +107,9 @@ size_t private_mesh_bytes(int dtype, int sum_mode, int64_t bins, int n_attrs, bo
 
 // Shared-memory bytes the privatised kernel needs for this mesh, or 0 if
 // the mesh does not fit.
-size_t private_smem_bytes(const BinArgs& a, int smem_optin);
+// Shared memory of the private strategy's mesh, 0 when it does not fit.
+// keys: -1 as a.st says; 0 / 1: f64 min/max without / with global key records.
+size_t private_smem_bytes(const BinArgs& a, int smem_optin, int keys = -1);
 cudaError_t launch_bin_private(const KernelCtx& kc, const BinArgs& a);
 cudaError_t launch_bin_global(const KernelCtx& kc, const BinArgs& a);
 size_t global_window_bytes(int win_cells, int n_attrs, bool do_sum);

@@ -171,11 +171,14 @@ size_t private_mesh_bytes(int dtype, int sum_mode, int64_t bins, int n_attrs, bo
     return private_bytes_for(dtype, dtype == BN_F64 ? kSumF64 : sum_mode, (int)bins, n_attrs, s, lo, hi);
 }
 
-size_t private_smem_bytes(const BinArgs& a, int smem_optin) {
+size_t private_smem_bytes(const BinArgs& a, int smem_optin, int keys) {
     const int64_t B = (int64_t)a.grid.ax[0].res * a.grid.ax[1].res;
     if (B > (1 << 20)) return 0;
-    size_t b = private_bytes_for(a.dtype, private_mode(a), (int)B, a.n_attrs, a.st.do_sum != 0,
-                                 a.st.do_min != 0, a.st.do_max != 0);
+    int mode = private_mode(a);
+    if (keys >= 0 && a.dtype == BN_F64)
+        mode = (keys && (a.st.do_min || a.st.do_max)) ? kSumF64Keys : kSumF64;
+    size_t b = private_bytes_for(a.dtype, mode, (int)B, a.n_attrs, a.st.do_sum != 0, a.st.do_min != 0,
+                                 a.st.do_max != 0);
     return b <= (size_t)smem_optin ? b : 0;
 }
 

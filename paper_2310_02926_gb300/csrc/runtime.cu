@@ -683,6 +683,11 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
             auto it = c->tuned.find(klass);
             if (it != c->tuned.end()) {
                 strat = it->second.strategy;
+                // a class spans a factor of two in bins: a mesh larger than the
+                // one the class was tuned on may not fit shared memory
+                const bool keys = dtype == BN_F64 && !accumulate && n_attrs > 0 && (want_min || want_max);
+                if (strat == BN_STRATEGY_PRIVATE && private_smem_bytes(args, c->smem_optin, keys ? 1 : 0) == 0)
+                    strat = BN_STRATEGY_GLOBAL;
                 if (!aggbits) args.aggregate = it->second.aggregate;
                 if (strat == BN_STRATEGY_GLOBAL && it->second.win_nx > 0 &&
                     it->second.win_x0 + it->second.win_nx <= grid->res[0] &&

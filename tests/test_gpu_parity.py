@@ -129,6 +129,21 @@ def test_min_max_with_tied_extremes(bn, ctx, strategy):
     check(w, run_gpu(ctx, w, flags=sflag(bn, strategy)), TOL_F64)
 
 
+def test_tuned_private_class_with_a_larger_mesh(bn):
+    """A shape class spans a factor of two in bins: after the class tunes to
+    the private strategy on a 64x64 mesh, a 90x90 mesh of the same class
+    (too large for one CTA's shared memory) still bins, on another strategy."""
+    c = bn.Context(0)
+    try:
+        for side in (64, 90):
+            w = workloads.uniform(1 << 23, seed=80 + side, res=side)
+            check(w, run_gpu(c, w), TOL_F64, label=f"{side}^2")
+            if side == 64:
+                assert "-> private" in bn.bn_context_autotune_report(c.handle)
+    finally:
+        c.close()
+
+
 def test_private_rejects_mesh_too_large_for_shared_memory(bn, ctx):
     w = workloads.plummer(10_000, seed=2, dtype=np.float64, res=1024)
     with pytest.raises(bn.BinningError) as e:
