@@ -74,6 +74,8 @@ extern "C" {
 #define BN_MAX_RES 65536
 #define BN_MAX_BINS (1 << 30)
 #define BN_HOST (-1)
+#define BN_MAX_MULTI_COLS 64  /* columns of one bn_bin_multi call */
+#define BN_MAX_MULTI_SPECS 256 /* binnings of one bn_bin_multi call */
 
 typedef enum bn_status {
     BN_OK = 0,
@@ -217,6 +219,17 @@ typedef struct bn_block {
     bn_result* out;
 } bn_block;
 
+/* One binning of a fused multi-grid pass (bn_bin_multi): the columns that
+ * are its coordinates and attributes (indices into the call's columns) and
+ * its mesh (explicit bounds). */
+typedef struct bn_grid_spec {
+    int32_t x, y;
+    int32_t n_attrs;
+    int32_t attrs[BN_MAX_ATTR];
+    int32_t reserved;
+    bn_grid grid;
+} bn_grid_spec;
+
 /* bn_options.flags */
 enum {
     /* Record a timing event pair around every hot-loop kernel launch (the
@@ -335,6 +348,29 @@ BN_API bn_status bn_bin_particles_static(const bn_buffer* x, const bn_buffer* y,
  */
 BN_API bn_status bn_bin_batch(bn_context* ctx, const bn_block* blocks, int n_blocks, uint32_t ops,
                        int sync, bn_request** req);
+
+/*
+ * Fused multi-grid pass: n_specs binnings of the same particles in one
+ * launch. Sec. 4.3 bins 10 variables in 9 coordinate systems every step (90
+ * binning operations, run one after another in the paper); here the
+ * particles are visited in tiles and every spec of a tile is binned before
+ * the next tile, so each column is read from memory once however many
+ * specs use it.
+ *   cols[0..n_cols)     1..BN_MAX_MULTI_COLS columns, same n and dtype,
+ *                       device or host memory as for bn_bin_particles
+ *   specs[0..n_specs)   1..BN_MAX_MULTI_SPECS binnings; column indices in
+ *                       [0, n_cols); explicit bounds only
+ *   ops                 as bn_bin_particles, without BN_OP_ACCUMULATE and
+ *                       strategy bits (aggregation bits apply)
+ *   outs[0..n_specs)    outs[k] receives spec k's result (bn_result rules)
+ * Each spec's result equals bn_bin_particles on its columns and grid
+ * (counts, min and max exactly; sums to within rounding order). Errors as
+ * bn_bin_particles; BN_ERR_INVALID_ARG for an index out of range,
+ * automatic bounds, accumulate or a strategy.
+ */
+BN_API bn_status bn_bin_multi(bn_context* ctx, const bn_buffer* cols, int n_cols,
+                              const bn_grid_spec* specs, int n_specs, uint32_t ops,
+                              bn_result* outs, int sync, bn_request** req);
 
 /*
  * Combine n_parts finalized results of one mesh into `out` (the cross-rank

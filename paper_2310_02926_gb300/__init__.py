@@ -23,8 +23,9 @@ from ._abi import (CTX_PROFILE, ALLOC_CUDA_ASYNC, ALLOC_EXTERNAL, ALLOC_HOST, AL
                    OP_MAX, OP_MIN, OP_SUM, STRATEGY_AUTO, STRATEGY_GLOBAL, STRATEGY_MASK,
                    STRATEGY_PRIVATE, STRATEGY_SORT, SUM_F32, SUM_F32C, SUM_F64, SUM_MASK, U64,
                    AGG_AUTO, AGG_ON, AGG_OFF, AGG_MASK,
-                   bn_block, bn_buffer, bn_grid, bn_options, bn_result, bn_server_options,
-                   bn_server_stats)
+                   MAX_MULTI_COLS, MAX_MULTI_SPECS,
+                   bn_block, bn_buffer, bn_grid, bn_grid_spec, bn_options, bn_result,
+                   bn_server_options, bn_server_stats)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libbinning.so")
@@ -217,6 +218,31 @@ def bn_bin_batch(ctx: int, blocks: Sequence[bn_block], ops: int, sync: bool = Tr
     arr = (bn_block * max(len(blocks), 1))(*blocks)
     req = ctypes.c_void_p()
     check(lib().bn_bin_batch(ctx, arr, len(blocks), ops, 1 if sync else 0,
+                             None if sync else ctypes.byref(req)))
+    return None if sync else req.value
+
+
+def grid_spec(x: int, y: int, attrs: Sequence[int], g: bn_grid) -> bn_grid_spec:
+    """One binning of bn_bin_multi: column indices of its coordinates and
+    attributes, and its mesh."""
+    sp = bn_grid_spec()
+    sp.x, sp.y = int(x), int(y)
+    sp.n_attrs = len(attrs)
+    for k, a in enumerate(attrs):
+        sp.attrs[k] = int(a)
+    sp.grid = g
+    return sp
+
+
+def bn_bin_multi(ctx: int, cols: Sequence, specs: Sequence[bn_grid_spec], ops: int,
+                 outs: Sequence[bn_result], sync: bool = True,
+                 stream: Optional[int] = None) -> Optional[int]:
+    """Fused multi-grid pass over torch columns; outs[k] receives spec k."""
+    carr = (bn_buffer * len(cols))(*[buffer(t, stream) for t in cols])
+    sarr = (bn_grid_spec * len(specs))(*specs)
+    oarr = (bn_result * len(outs))(*outs)
+    req = ctypes.c_void_p()
+    check(lib().bn_bin_multi(ctx, carr, len(cols), sarr, len(specs), ops, oarr, 1 if sync else 0,
                              None if sync else ctypes.byref(req)))
     return None if sync else req.value
 

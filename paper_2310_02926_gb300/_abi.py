@@ -80,6 +80,15 @@ class bn_block(ctypes.Structure):
                 ("grid", bn_grid), ("out", ctypes.POINTER(bn_result))]
 
 
+class bn_grid_spec(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_int32), ("y", ctypes.c_int32), ("n_attrs", ctypes.c_int32),
+                ("attrs", ctypes.c_int32 * MAX_ATTR), ("reserved", ctypes.c_int32),
+                ("grid", bn_grid)]
+
+
+MAX_MULTI_COLS = 64
+MAX_MULTI_SPECS = 256
+
 CTX_PROFILE = 1
 
 
@@ -123,6 +132,8 @@ PROTOTYPES = {
                                     ctypes.POINTER(bn_result), P, ctypes.c_int]),
     "bn_bin_batch": (S, [P, ctypes.POINTER(bn_block), ctypes.c_int, ctypes.c_uint32,
                          ctypes.c_int, PP]),
+    "bn_bin_multi": (S, [P, ctypes.POINTER(bn_buffer), ctypes.c_int, ctypes.POINTER(bn_grid_spec),
+                         ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(bn_result), ctypes.c_int, PP]),
     "bn_merge_results": (S, [P, ctypes.POINTER(bn_result), ctypes.c_int, ctypes.c_int32,
                              ctypes.c_int, ctypes.c_int64, ctypes.c_uint32,
                              ctypes.POINTER(bn_result), ctypes.c_int, PP]),

@@ -105,6 +105,23 @@ cudaError_t launch_batch_finalize(const KernelCtx& kc, const BatchBlock* dev_blo
                                   const int64_t* dev_bin_start, int nblk, int64_t total_bins);
 size_t private_mesh_bytes(int dtype, int sum_mode, int64_t bins, int n_attrs, bool s, bool lo, bool hi);
 
+// One binning of a fused multi-grid pass (k_multi.cu), in device memory.
+struct MultiSpec {
+    const GridDesc* grid;  // device descriptor (f64: with its edge keys)
+    const void* x;
+    const void* y;
+    const void* a[kMaxAttr];
+    int32_t n_attrs;
+    int32_t aggregate;
+    StateDesc st;
+};
+
+// Particles per tile of the fused pass: every spec of a tile is binned
+// before the next tile, while the tile's columns are still in L1/L2.
+constexpr int kMultiTile = 1024;
+cudaError_t launch_bin_multi(const KernelCtx& kc, int dtype, const MultiSpec* dev_specs, int n_specs,
+                             int64_t n);
+
 // Shared-memory bytes the privatised kernel needs for this mesh, or 0 if
 // the mesh does not fit.
 // Shared memory of the private strategy's mesh, 0 when it does not fit.

@@ -944,6 +944,167 @@ bn_status bn::complete_sync(bn_request* r, int sync, bn_request** req) {
     return BN_OK;
 }
 
+// Fused multi-grid pass (bn_bin_multi): every column is staged or taken in
+// place once, each spec gets its mesh descriptor, outputs and initial state
+// as a bn_bin_particles call would, and one k_bin_multi launch bins them all.
+static bn_status enqueue_multi(bn_context* c, Plan& plan, const bn_buffer* cols, int n_cols,
+                               const bn_grid_spec* specs, int n_specs, uint32_t ops, bn_result* outs,
+                               int* status_dev) {
+    const int dtype = cols[0].dtype;
+    const int64_t n = cols[0].n;
+    if (dtype != BN_F32 && dtype != BN_F64) return fail(BN_ERR_INVALID_ARG, "bn_bin_multi: dtype must be BN_F32 or BN_F64");
+    for (int i = 0; i < n_cols; ++i) {
+        bn_status st = validate_buffer(c, &cols[i], n, dtype, "column");
+        if (st != BN_OK) return st;
+    }
+    if (ops & BN_OP_ACCUMULATE) return fail(BN_ERR_INVALID_ARG, "bn_bin_multi: BN_OP_ACCUMULATE is not supported");
+    if (ops & BN_STRATEGY_MASK) return fail(BN_ERR_INVALID_ARG, "bn_bin_multi: the fused pass takes no strategy");
+    if ((ops & BN_AGG_MASK) == BN_AGG_MASK) return fail(BN_ERR_INVALID_ARG, "unknown aggregation mode in ops");
+    if ((ops & BN_SUM_MASK) == (3u << 8)) return fail(BN_ERR_INVALID_ARG, "unknown sum mode in ops");
+    const bool want_avg = (ops & BN_OP_AVG) != 0;
+    const bool want_sum = (ops & BN_OP_SUM) != 0;
+    const bool want_min = (ops & BN_OP_MIN) != 0;
+    const bool want_max = (ops & BN_OP_MAX) != 0;
+    const bool want_count = (ops & BN_OP_COUNT) != 0;
+    const bool attr_ops = want_sum || want_avg || want_min || want_max;
+    const uint32_t agg = ops & BN_AGG_MASK;
+    for (int k = 0; k < n_specs; ++k) {
+        const bn_grid_spec& sp = specs[k];
+        if (sp.x < 0 || sp.x >= n_cols || sp.y < 0 || sp.y >= n_cols)
+            return fail(BN_ERR_INVALID_ARG, "bn_bin_multi: spec %d: coordinate column out of range", k);
+        if (sp.n_attrs < 0 || sp.n_attrs > BN_MAX_ATTR)
+            return fail(BN_ERR_INVALID_ARG, "bn_bin_multi: spec %d: n_attrs = %d outside [0, %d]", k, sp.n_attrs, BN_MAX_ATTR);
+        for (int a = 0; a < sp.n_attrs; ++a)
+            if (sp.attrs[a] < 0 || sp.attrs[a] >= n_cols)
+                return fail(BN_ERR_INVALID_ARG, "bn_bin_multi: spec %d: attribute column out of range", k);
+        if (sp.grid.auto_bounds) return fail(BN_ERR_INVALID_ARG, "bn_bin_multi: spec %d: automatic bounds are not supported", k);
+    }
+    std::vector<const void*> colp((size_t)n_cols, nullptr);
+    for (int i = 0; i < n_cols; ++i) {
+        bn_status st = plan.column(&cols[i], dtype, &colp[i]);
+        if (st != BN_OK) return st;
+    }
+    const KernelCtx kc = plan.kc();
+    std::vector<MultiSpec> hs((size_t)n_specs);
+    for (int k = 0; k < n_specs; ++k) {
+        const bn_grid_spec& sp = specs[k];
+        MultiSpec& m = hs[k];
+        memset(&m, 0, sizeof m);
+        GridDesc gd;
+        bn_status st = make_grid_desc(&sp.grid, dtype, &gd);
+        if (st != BN_OK) return st;
+        const int64_t B = (int64_t)sp.grid.res[0] * sp.grid.res[1];
+        GridDesc* dg = static_cast<GridDesc*>(plan.alloc(sizeof(GridDesc)));
+        long long* e0 = nullptr;
+        long long* e1 = nullptr;
+        if (dtype == BN_F64) {
+            e0 = static_cast<long long*>(plan.alloc(sizeof(long long) * (sp.grid.res[0] + 1)));
+            e1 = static_cast<long long*>(plan.alloc(sizeof(long long) * (sp.grid.res[1] + 1)));
+        }
+        if (!dg || (dtype == BN_F64 && (!e0 || !e1))) return cuda_fail(plan.err, "cudaMallocAsync(grid)");
+        cudaError_t e = launch_grid_setup(kc, dtype, gd, nullptr, dg, e0, e1, nullptr, status_dev);
+        if (e != cudaSuccess) return cuda_fail(e, "grid setup kernel");
+        const int A = attr_ops ? sp.n_attrs : 0;
+        m.grid = dg;
+        m.x = colp[sp.x];
+        m.y = colp[sp.y];
+        for (int a = 0; a < A; ++a) m.a[a] = colp[sp.attrs[a]];
+        m.n_attrs = A;
+        m.aggregate = agg == BN_AGG_ON ? 1 : agg == BN_AGG_OFF ? 0 : (B <= 65536 ? 1 : 0);
+        StateDesc& sd = m.st;
+        sd.bins = B;
+        sd.n_attrs = A;
+        sd.do_sum = (want_sum || want_avg) ? 1 : 0;
+        sd.do_min = want_min ? 1 : 0;
+        sd.do_max = want_max ? 1 : 0;
+        sd.do_avg = want_avg ? 1 : 0;
+        bn_result* out = &outs[k];
+        void* p = nullptr;
+        st = plan.output(&out->count, want_count, B, BN_U64, false, &p);
+        if (st != BN_OK) return st;
+        sd.count = static_cast<unsigned long long*>(p);
+        for (int a = 0; a < A; ++a) {
+            if (sd.do_sum) {
+                st = plan.output(&out->sum[a], want_sum, B, BN_F64, false, &p);
+                if (st != BN_OK) return st;
+                sd.sum[a] = static_cast<double*>(p);
+            }
+            if (want_min) {
+                st = plan.output(&out->min[a], true, B, dtype, false, &p);
+                if (st != BN_OK) return st;
+                sd.mn[a] = p;
+            }
+            if (want_max) {
+                st = plan.output(&out->max[a], true, B, dtype, false, &p);
+                if (st != BN_OK) return st;
+                sd.mx[a] = p;
+            }
+            if (want_avg) {
+                st = plan.output(&out->avg[a], true, B, BN_F64, false, &p);
+                if (st != BN_OK) return st;
+                sd.avg[a] = static_cast<double*>(p);
+            }
+        }
+        e = launch_init_state(kc, dtype, sd, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    }
+    // the descriptors; a pageable source is copied out before the call returns
+    MultiSpec* ds = static_cast<MultiSpec*>(plan.alloc(sizeof(MultiSpec) * (size_t)n_specs));
+    if (!ds) return cuda_fail(plan.err, "cudaMallocAsync(specs)");
+    cudaError_t e = cudaMemcpyAsync(ds, hs.data(), sizeof(MultiSpec) * (size_t)n_specs,
+                                    cudaMemcpyHostToDevice, plan.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy specs");
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (c->profile && cudaEventCreate(&t0) == cudaSuccess && cudaEventCreate(&t1) == cudaSuccess)
+        cudaEventRecord(t0, plan.stream);
+    e = launch_bin_multi(kc, dtype, ds, n_specs, n);
+    if (t1) {
+        cudaEventRecord(t1, plan.stream);
+        std::lock_guard<std::mutex> lk(c->prof_mu);
+        c->prof_pairs.emplace_back(t0, t1);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "fused multi-grid kernel");
+    if (want_avg)
+        for (int k = 0; k < n_specs; ++k) {
+            e = launch_finalize(kc, hs[k].st, dtype);
+            if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
+        }
+    plan.strategy = BN_STRATEGY_GLOBAL;
+    return BN_OK;
+}
+
+extern "C" bn_status bn_bin_multi(bn_context* c, const bn_buffer* cols, int n_cols, const bn_grid_spec* specs,
+                                  int n_specs, uint32_t ops, bn_result* outs, int sync, bn_request** req) {
+    g_err.clear();
+    if (!c || !cols || !specs || !outs) return fail(BN_ERR_INVALID_ARG, "bn_bin_multi: NULL argument");
+    if (n_cols < 1 || n_cols > BN_MAX_MULTI_COLS)
+        return fail(BN_ERR_INVALID_ARG, "bn_bin_multi: n_cols = %d outside [1, %d]", n_cols, BN_MAX_MULTI_COLS);
+    if (n_specs < 1 || n_specs > BN_MAX_MULTI_SPECS)
+        return fail(BN_ERR_INVALID_ARG, "bn_bin_multi: n_specs = %d outside [1, %d]", n_specs, BN_MAX_MULTI_SPECS);
+    if (!sync && !req) return fail(BN_ERR_INVALID_ARG, "bn_bin_multi: asynchronous call needs req");
+    if (req) *req = nullptr;
+    DeviceGuard g(c->device);
+    std::lock_guard<std::mutex> lk(c->enqueue_mu);
+    bn_request* r = new_request(c);
+    if (!r) return fail(BN_ERR_NO_MEMORY, "bn_bin_multi: no request slot");
+    Plan plan(c);
+    bn_status st = enqueue_multi(c, plan, cols, n_cols, specs, n_specs, ops, outs, c->status_dev + r->slot);
+    if (st == BN_OK) st = plan.finish(r);
+    if (st != BN_OK) {
+        std::string msg = g_err;
+        plan.free_temps();
+        cudaEventRecord(r->done, c->stream);
+        r->host_status = st;
+        bn_request_release(r);
+        g_err = msg;
+        return st;
+    }
+    for (int i = 0; i < n_cols; ++i)
+        if (cols[i].deleter) r->deleters.push_back({cols[i].deleter, cols[i].ptr, cols[i].deleter_ctx});
+    c->last_strategy = BN_STRATEGY_GLOBAL;
+    return complete_sync(r, sync, req);
+}
+
 extern "C" bn_status bn_bin_particles(bn_context* c, const bn_buffer* x, const bn_buffer* y,
                                       const bn_buffer* attrs, int n_attrs, const bn_grid* grid,
                                       uint32_t ops, bn_result* out, int sync, bn_request** req) {

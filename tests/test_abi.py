@@ -35,10 +35,11 @@ def test_library_exports_every_header_entry_point(bn):
 def test_struct_layouts_match_header(bn, tmp_path):
     from paper_2310_02926_gb300 import _abi
     src = tmp_path / "sz.c"
-    structs = ["bn_buffer", "bn_grid", "bn_result", "bn_block", "bn_options",
+    structs = ["bn_buffer", "bn_grid", "bn_result", "bn_block", "bn_grid_spec", "bn_options",
                "bn_server_options", "bn_server_stats"]
     body = "\n".join(f'printf("%zu\\n", sizeof({s}));' for s in structs)
     offs = [("bn_buffer", "stream"), ("bn_buffer", "deleter"), ("bn_block", "grid"),
+            ("bn_grid_spec", "grid"),
             ("bn_block", "out"), ("bn_result", "bounds"), ("bn_grid", "res")]
     body += "\n" + "\n".join(f'printf("%zu\\n", offsetof({s}, {f}));' for s, f in offs)
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "binning.h"\n'
@@ -70,6 +71,10 @@ def test_constants_match_header(bn):
         m = re.search(name + r"\s*=\s*(\d+)u?\s*<<\s*(\d+)", hdr)
         assert m, name
         assert getattr(_abi, name[3:]) == int(m.group(1)) << int(m.group(2)), name
+    for name, val in (("BN_MAX_MULTI_COLS", _abi.MAX_MULTI_COLS), ("BN_MAX_MULTI_SPECS", _abi.MAX_MULTI_SPECS),
+                      ("BN_MAX_ATTR", _abi.MAX_ATTR)):
+        m = re.search(r"#define\s+" + name + r"\s+(\d+)", hdr)
+        assert m and int(m.group(1)) == val, name
     for name, val in (("BN_ERR_DEGENERATE", _abi.ERR_DEGENERATE), ("BN_ERR_BUDGET", _abi.ERR_BUDGET),
                       ("BN_ERR_TIMEOUT", _abi.ERR_TIMEOUT), ("BN_NOT_READY", _abi.NOT_READY)):
         m = re.search(name + r"\s*=\s*(-?\d+)", hdr)

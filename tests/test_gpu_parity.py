@@ -657,3 +657,73 @@ def test_gaussians_f32_full_size(bn, ctx):
     """2^27 f32 particles from 16 Gaussians on a 4096x4096 mesh (compensated sums)."""
     w = workloads.gaussians(2 ** 27, seed=0, res=4096)
     check(w, run_gpu(ctx, w), TOL_F32C, label="gaussians full")
+
+
+# ------------------------------------------------------------------ fused multi-grid pass
+def _multi_columns(n, seed, dtype):
+    """Positions and velocities of a Plummer-like cloud plus two scalars."""
+    rng = np.random.default_rng(seed)
+    pos = rng.standard_normal((3, n)) * 2.0
+    vel = rng.standard_normal((3, n))
+    mass = rng.uniform(1.0, 2.0, n)
+    energy = 0.5 * mass * (vel ** 2).sum(0)
+    return [c.astype(dtype) for c in (*pos, *vel, mass, energy)]
+
+
+MULTI_SPECS = [  # (x, y, attrs, lo, hi, res): columns 0-2 x,y,z, 3-5 vx,vy,vz, 6 mass, 7 energy
+    (0, 1, [6, 7], (-6.0, -6.0), (6.0, 6.0), (64, 64)),
+    (0, 2, [6], (-6.0, -6.0), (6.0, 6.0), (50, 33)),
+    (1, 2, [7, 3, 4], (-4.0, -5.0), (4.0, 5.0), (128, 96)),
+    (3, 4, [6, 7], (-3.0, -3.0), (3.0, 3.0), (40, 40)),
+    (0, 1, [0, 1, 6], (-1.0, -1.0), (1.0, 1.0), (300, 300)),   # coordinates as attributes
+    (5, 6, [], (-2.0, 1.0), (2.0, 2.0), (7, 5)),               # count only, mass on an axis
+]
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_multi_grid_matches_each_binning(bn, ctx, dtype, where):
+    """bn_bin_multi: each spec's result equals binning its columns alone."""
+    n = 70_001  # not a multiple of the tile
+    cols = _multi_columns(n, 90, dtype)
+    tcols = [torch.from_numpy(c) for c in cols]
+    if where == "device":
+        tcols = [t.cuda() for t in tcols]
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    specs, outs, keep = [], [], []
+    for (x, y, attrs, lo, hi, res) in MULTI_SPECS:
+        specs.append(bn.grid_spec(x, y, attrs, bn.grid(lo, hi, res)))
+        o = bn.alloc_outputs(len(attrs), res[0] * res[1], tdt, torch.device("cuda"))
+        keep.append(o)
+        outs.append(bn.result_struct(o))
+    bn.bn_bin_multi(ctx.handle, tcols, specs, bn.OP_ALL, outs)
+    torch.cuda.synchronize()
+    for k, (x, y, attrs, lo, hi, res) in enumerate(MULTI_SPECS):
+        w = workloads.Workload(f"spec{k}", cols[x], cols[y], [cols[a] for a in attrs], lo, hi, res)
+        got = to_numpy_result(keep[k])
+        if attrs:
+            check(w, got, TOL_F64, label=f"spec {k}")
+        else:
+            ref = oracle.bin_workload(w, False)
+            np.testing.assert_array_equal(got["count"], ref["count"], err_msg=f"spec {k}")
+
+
+def test_multi_grid_rejects_bad_arguments(bn, ctx):
+    cols = [torch.zeros(10, dtype=torch.float64, device="cuda") for _ in range(3)]
+    g = bn.grid((0, 0), (1, 1), (4, 4))
+    o = bn.alloc_outputs(1, 16, torch.float64, torch.device("cuda"))
+    r = bn.result_struct(o)
+    bad = [
+        ([bn.grid_spec(0, 3, [1], g)], bn.OP_ALL),                      # column out of range
+        ([bn.grid_spec(0, 1, [7], g)], bn.OP_ALL),                      # attribute out of range
+        ([bn.grid_spec(0, 1, [2], bn.grid((0, 0), (1, 1), (4, 4), auto_bounds=True))], bn.OP_ALL),
+        ([bn.grid_spec(0, 1, [2], g)], bn.OP_ALL | bn.OP_ACCUMULATE),
+        ([bn.grid_spec(0, 1, [2], g)], bn.OP_ALL | bn.STRATEGY_PRIVATE),
+    ]
+    for specs, ops in bad:
+        with pytest.raises(bn.BinningError) as e:
+            bn.bn_bin_multi(ctx.handle, cols, specs, ops, [r])
+        assert e.value.code == bn.ERR_INVALID_ARG
+    odd = [cols[0], cols[1], torch.zeros(9, dtype=torch.float64, device="cuda")]
+    with pytest.raises(bn.BinningError):
+        bn.bn_bin_multi(ctx.handle, odd, [bn.grid_spec(0, 1, [2], g)], bn.OP_ALL, [r])
