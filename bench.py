@@ -57,6 +57,10 @@ WORKLOADS = {
     "batch256": ("batch", 256, 0, 2, "f32",
                  "{n} blocks of log-uniform 1e3..1e7 f32 particles (uniform or Plummer per block), "
                  "square meshes log-uniform 32..2048, 2 attributes, one bn_bin_batch call"),
+    "multigrid": ("multigrid", 2 ** 22, 256, 10, "f64",
+                  "{n:,} f64 particles of a Plummer snapshot (positions, velocities, 4 derived "
+                  "scalars), 10 variables binned in 9 coordinate systems on 256x256 meshes, "
+                  "one fused bn_bin_multi call vs 9 bn_bin_particles calls"),
     "serving": ("serving", 10_000, 0, 3, "f32",
                 "Poisson stream of {n:,} requests (mean 2 ms apart, log-uniform 1e4..2e7 f32 "
                 "particles, meshes 64^2..1024^2) under a 40 GB budget beside a direct-sum "
@@ -361,6 +365,106 @@ def run_batch(args, n_blocks):
     return 0
 
 
+def run_multigrid(args, n):
+    """Fused multi-grid pass: 10 variables in 9 coordinate systems (Sec. 4.3)
+    binned by one bn_bin_multi call, against the same 90 binnings as 9
+    bn_bin_particles calls. Both read the columns from HBM."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2310_02926_gb300 as bn
+    import workloads
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = bn.Context(0, stream=stream.cuda_stream)
+    cols = workloads.phase_space(n, seed=0)
+    names = list(cols)
+    res = (args.multigrid_res, args.multigrid_res)
+    with torch.cuda.stream(stream):
+        tcols = [torch.from_numpy(cols[k]).to(dev) for k in names]
+        specs, outs, keep, sep = [], [], [], []
+        variables = [names.index(v) for v in workloads.PHASE_SPACE_VARIABLES[:args.multigrid_vars]]
+        for (a, b) in workloads.PHASE_SPACE_SYSTEMS:
+            ha, hb = workloads.PHASE_SPACE_BOUNDS[a], workloads.PHASE_SPACE_BOUNDS[b]
+            g = bn.grid((-ha, -hb), (ha, hb), res)
+            specs.append(bn.grid_spec(names.index(a), names.index(b), variables, g))
+            o = bn.alloc_outputs(len(variables), res[0] * res[1], torch.float64, dev)
+            keep.append(o)
+            outs.append(bn.result_struct(o))
+            o2 = bn.alloc_outputs(len(variables), res[0] * res[1], torch.float64, dev)
+            sep.append((names.index(a), names.index(b), g, bn.result_struct(o2), o2))
+
+        def timed(fn, steps, warm):
+            for _ in range(warm):
+                fn()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = ctx.launches
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / steps, (ctx.launches - l0) // steps
+
+        def fused():
+            r = bn.bn_bin_multi(ctx.handle, tcols, specs, bn.OP_ALL, outs, sync=False)
+            bn.bn_request_release(r)
+
+        sep_ops = bn.OP_ALL | {"auto": 0, "global": bn.STRATEGY_GLOBAL, "private": bn.STRATEGY_PRIVATE,
+                               "sort": bn.STRATEGY_SORT}[args.strategy]
+
+        def separate():
+            for (ia, ib, g, r, _) in sep:
+                q = bn.bn_bin_particles(ctx.handle, tcols[ia], tcols[ib], [tcols[v] for v in variables],
+                                        g, sep_ops, r, sync=False)
+                bn.bn_request_release(q)
+
+        ms_f, launches_f = timed(fused, args.steps, args.warmup)
+        ms_s, launches_s = timed(separate, max(1, args.steps // 4), args.warmup)
+    B = res[0] * res[1]
+    nv = len(variables)
+    bytes_in = n * 8 * len(names)                     # every column once
+    bytes_out = len(specs) * B * (8 + nv * 4 * 8)     # count, and sum/min/max/avg per variable
+    hbm, peak_src = peaks()
+    achieved = (bytes_in + bytes_out) / (ms_f / 1e3) / 1e9
+    line = {"metric": METRIC, "value": n / (ms_f / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_f,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS["multigrid"][5].format(n=n).replace(
+                           "10 variables", f"{nv} variables").replace("256x256", f"{res[0]}x{res[1]}"),
+                       "name": "multigrid",
+                       "n_particles": n, "columns": len(names), "systems": len(specs),
+                       "variables": nv, "grid": list(res), "l2": "inputs 0.44 GB > L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": "whole step (fused pass + per-spec set-up and finalise)",
+                         "algorithmic_bytes_per_launch": bytes_in + bytes_out,
+                         "peak_source": peak_src},
+            "fused": {"ms": ms_f, "particles_per_s": n / (ms_f / 1e3), "gpu_launches_per_step": launches_f},
+            "separate": {"ms": ms_s, "particles_per_s": n / (ms_s / 1e3), "gpu_launches_per_step": launches_s},
+            "speedup_fused_vs_separate": ms_s / ms_f,
+            "separate_strategy": args.strategy,
+            "autotuner": bn.bn_context_autotune_report(ctx.handle).strip().splitlines(),
+            "gpu_launches": launches_f * args.steps, "e2e": None, "cpu_baseline": None}
+    if args.check:
+        worst, exact = 0.0, True
+        for k, (a, b) in enumerate(workloads.PHASE_SPACE_SYSTEMS):
+            ha, hb = workloads.PHASE_SPACE_BOUNDS[a], workloads.PHASE_SPACE_BOUNDS[b]
+            w = workloads.Workload(f"{a}-{b}", cols[a], cols[b],
+                                   [cols[v] for v in workloads.PHASE_SPACE_VARIABLES[:args.multigrid_vars]],
+                                   (-ha, -hb), (ha, hb), res)
+            e = compare_with_oracle(w, dict(keep[k]), bn)
+            worst = max(worst, e["sum_rel_err_max"])
+            exact = exact and all(v for kk, v in e.items() if kk.endswith("_exact"))
+        line["errors_vs_oracle"] = {"exact_count_min_max": exact, "sum_rel_err_max": worst}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_serving(args, n_requests):
     """Serving: a Poisson stream of requests submitted to a bn_server at
     their arrival times while the n-body producer runs on its own stream;
@@ -507,6 +611,10 @@ def main():
     ap.add_argument("--no-producer", action="store_true", help="serving without the producer")
     ap.add_argument("--ops", default="all", choices=["all", "count", "count+sum", "count+minmax"],
                     help="reductions to compute (all = count/sum/min/max/avg, the benchmark's)")
+    ap.add_argument("--multigrid-vars", type=int, default=10, choices=range(1, 11),
+                    help="multigrid workload: variables binned in every coordinate system")
+    ap.add_argument("--multigrid-res", type=int, default=256,
+                    help="multigrid workload: mesh side of every coordinate system")
     ap.add_argument("--check", action="store_true",
                     help="compare the last step with the CPU oracle and report per-bin errors")
     args = ap.parse_args()
@@ -519,6 +627,8 @@ def main():
         return run_batch(args, N_PART)
     if args.workload == "serving":
         return run_serving(args, N_PART)
+    if args.workload == "multigrid":
+        return run_multigrid(args, N_PART)
 
     import numpy as np
     import torch

@@ -118,7 +118,7 @@ struct MultiSpec {
 
 // Particles per tile of the fused pass: every spec of a tile is binned
 // before the next tile, while the tile's columns are still in L1/L2.
-constexpr int kMultiTile = 1024;
+constexpr int kMultiTile = 2048;
 cudaError_t launch_bin_multi(const KernelCtx& kc, int dtype, const MultiSpec* dev_specs, int n_specs,
                              int64_t n);
 

@@ -20,6 +20,18 @@ namespace bn {
 template <typename T>
 __global__ void __launch_bounds__(256) k_bin_multi(const MultiSpec* __restrict__ specs, int n_specs,
                                                    int64_t n) {
+    // every spec's binner, built once per CTA
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ MultiSpec cur;
+    Binner<T>* binners = reinterpret_cast<Binner<T>*>(smem);
+    for (int s = threadIdx.x; s < n_specs; s += blockDim.x) {
+        const GridDesc g = *specs[s].grid;
+        Binner<T> bnr;
+        if (g.valid) bnr.init(g);
+        else bnr.rx = -1;  // marks an invalid mesh: the spec is skipped
+        binners[s] = bnr;
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = threadIdx.x & ~31;
     const int64_t ntiles = (n + kMultiTile - 1) / kMultiTile;
@@ -27,11 +39,19 @@ __global__ void __launch_bounds__(256) k_bin_multi(const MultiSpec* __restrict__
         const int64_t i0 = t * kMultiTile;
         const int64_t i1 = (n - i0) < kMultiTile ? n : i0 + kMultiTile;
         for (int s = 0; s < n_specs; ++s) {
-            const MultiSpec& sp = specs[s];
-            const GridDesc g = *sp.grid;
-            if (!g.valid) continue;
-            Binner<T> binner;
-            binner.init(g);
+            const Binner<T>& binner = binners[s];
+            if (binner.rx < 0) continue;
+            // the spec's descriptor in shared memory: its pointers cannot alias
+            // the global atomics, so they are not reloaded around every commit
+            __syncthreads();
+            {
+                const int* src = reinterpret_cast<const int*>(specs + s);
+                int* dst = reinterpret_cast<int*>(&cur);
+                for (int w = threadIdx.x; w < (int)(sizeof(MultiSpec) / sizeof(int)); w += blockDim.x)
+                    dst[w] = src[w];
+            }
+            __syncthreads();
+            const MultiSpec& sp = cur;
             const T* __restrict__ X = static_cast<const T*>(sp.x);
             const T* __restrict__ Y = static_cast<const T*>(sp.y);
             const int A = sp.n_attrs;
@@ -56,10 +76,14 @@ cudaError_t launch_bin_multi(const KernelCtx& kc, int dtype, const MultiSpec* de
     if (n <= 0 || n_specs <= 0) return cudaSuccess;
     const int block = 256;
     int64_t grid = (n + kMultiTile - 1) / kMultiTile;
-    const int64_t cap = (int64_t)kc.num_sms * 8;
+    // 4 CTAs per SM: a tile's columns (kMultiTile x columns x 8 B) stay within
+    // a CTA's share of L2 between the specs that read them
+    const int64_t cap = (int64_t)kc.num_sms * 4;
     if (grid > cap) grid = cap;
-    if (dtype == BN_F64) k_bin_multi<double><<<(int)grid, block, 0, kc.stream>>>(dev_specs, n_specs, n);
-    else k_bin_multi<float><<<(int)grid, block, 0, kc.stream>>>(dev_specs, n_specs, n);
+    if (dtype == BN_F64)
+        k_bin_multi<double><<<(int)grid, block, sizeof(Binner<double>) * n_specs, kc.stream>>>(dev_specs, n_specs, n);
+    else
+        k_bin_multi<float><<<(int)grid, block, sizeof(Binner<float>) * n_specs, kc.stream>>>(dev_specs, n_specs, n);
     kc.count_launch();
     return cudaGetLastError();
 }

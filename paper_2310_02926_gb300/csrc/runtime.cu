@@ -1010,7 +1010,9 @@ static bn_status enqueue_multi(bn_context* c, Plan& plan, const bn_buffer* cols,
         m.y = colp[sp.y];
         for (int a = 0; a < A; ++a) m.a[a] = colp[sp.attrs[a]];
         m.n_attrs = A;
-        m.aggregate = agg == BN_AGG_ON ? 1 : agg == BN_AGG_OFF ? 0 : (B <= 65536 ? 1 : 0);
+        // combining a warp's same-bin lanes (__match_any_sync) only on request:
+        // there is no trial here to show it pays
+        m.aggregate = agg == BN_AGG_ON ? 1 : 0;
         StateDesc& sd = m.st;
         sd.bins = B;
         sd.n_attrs = A;
@@ -1045,6 +1047,13 @@ static bn_status enqueue_multi(bn_context* c, Plan& plan, const bn_buffer* cols,
                 sd.avg[a] = static_cast<double*>(p);
             }
         }
+        // min/max as key records (one or two 256-bit loads per particle for
+        // all attributes), written to the outputs by the finalise kernel
+        if (A > 0 && (want_min || want_max)) {
+            sd.mmk = plan.alloc((size_t)key_record_pairs(A, (int)dtype_size(dtype)) * B * 2 *
+                                dtype_size(dtype));
+            if (!sd.mmk) return cuda_fail(plan.err, "cudaMallocAsync(min/max keys)");
+        }
         e = launch_init_state(kc, dtype, sd, nullptr);
         if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     }
@@ -1064,8 +1073,8 @@ static bn_status enqueue_multi(bn_context* c, Plan& plan, const bn_buffer* cols,
         c->prof_pairs.emplace_back(t0, t1);
     }
     if (e != cudaSuccess) return cuda_fail(e, "fused multi-grid kernel");
-    if (want_avg)
-        for (int k = 0; k < n_specs; ++k) {
+    for (int k = 0; k < n_specs; ++k)
+        if (want_avg || hs[k].st.mmk) {
             e = launch_finalize(kc, hs[k].st, dtype);
             if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
         }

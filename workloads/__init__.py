@@ -148,6 +148,34 @@ def gaussians(n: int = 2 ** 27, seed: int = 0, dtype=np.float32, res: int = 4096
                     cols[0], cols[1], cols[2:], (0.0, 0.0), (1.0, 1.0), (res, res))
 
 
+# The 9 coordinate systems of the fused multi-grid workload: three position
+# planes, three velocity planes and three position-velocity pairs.
+PHASE_SPACE_SYSTEMS = [("x", "y"), ("x", "z"), ("y", "z"), ("vx", "vy"), ("vx", "vz"), ("vy", "vz"),
+                       ("x", "vx"), ("y", "vy"), ("z", "vz")]
+# The 10 variables binned in every system.
+PHASE_SPACE_VARIABLES = ["mass", "vx", "vy", "vz", "speed", "ke", "r", "phi", "lz", "ly"]
+PHASE_SPACE_BOUNDS = {"x": 10.0, "y": 10.0, "z": 10.0, "vx": 4.0, "vy": 4.0, "vz": 4.0}
+
+
+def phase_space(n: int = 2 ** 22, seed: int = 0, dtype=np.float64):
+    """An N-body snapshot for the fused multi-grid workload (the in situ
+    step of Sec. 4.3: 10 variables binned in 9 coordinate systems). Plummer
+    positions (a = 1, r < 10) in 3D, isotropic N(0,1) velocities, mass
+    U[1,2], and derived scalars: speed, kinetic energy, radius, a softened
+    potential -m / sqrt(r^2 + 1), and angular momenta lz = x vy - y vx,
+    ly = z vx - x vz. Returns a dict name -> column."""
+    rng = _rng(seed)
+    x, y, z = _plummer_xy(rng, n)
+    vx, vy, vz = rng.standard_normal((3, n))
+    mass = rng.uniform(1.0, 2.0, n)
+    speed = np.sqrt(vx * vx + vy * vy + vz * vz)
+    r = np.sqrt(x * x + y * y + z * z)
+    cols = {"x": x, "y": y, "z": z, "vx": vx, "vy": vy, "vz": vz, "mass": mass, "speed": speed,
+            "ke": 0.5 * mass * speed * speed, "r": r, "phi": -mass / np.sqrt(r * r + 1.0),
+            "lz": x * vy - y * vx, "ly": z * vx - x * vz}
+    return {k: np.ascontiguousarray(v, dtype=dtype) for k, v in cols.items()}
+
+
 @dataclasses.dataclass
 class BatchPlan:
     """Per-block parameters of a batch; ``block(k)`` draws block k's data."""
