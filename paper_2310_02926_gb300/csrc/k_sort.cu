@@ -224,9 +224,20 @@ __global__ void __launch_bounds__(1024) k_sort_scatter(BinArgs args, SortDesc sd
     const int n_in = hist[NB];
     // reserve this tile's run in every bucket it feeds: sorted record i of
     // bucket k goes to slot gpos[k] + i
-    for (int k = threadIdx.x; k < NB; k += blockDim.x) {
-        const int c = hist[k + 1] - hist[k];
-        gpos[k] = c ? (int)atomicAdd(&sd.cursor[k], (unsigned)c) - hist[k] : 0;
+    // (four reservations in flight per thread: their L2 round trips overlap)
+    for (int k0 = threadIdx.x; k0 < NB; k0 += 4 * blockDim.x) {
+        int got[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = k0 + u * blockDim.x;
+            const int c = k < NB ? hist[k + 1] - hist[k] : 0;
+            got[u] = c ? (int)atomicAdd(&sd.cursor[k], (unsigned)c) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = k0 + u * blockDim.x;
+            if (k < NB) gpos[k] = got[u] - hist[k];
+        }
     }
     // sorted position of each particle (reusing slot); key and bucket now,
     // attributes column by column in groups of 8
