@@ -119,8 +119,11 @@ struct MultiSpec {
 // Particles per tile of the fused pass: every spec of a tile is binned
 // before the next tile, while the tile's columns are still in L1/L2.
 constexpr int kMultiTile = 2048;
-cudaError_t launch_bin_multi(const KernelCtx& kc, int dtype, const MultiSpec* dev_specs, int n_specs,
-                             int64_t n);
+// dev_specs holds n_groups runs of specs; run g has group_size[g] specs of
+// group_attrs[g] attributes each and gets one launch (the kernel is compiled
+// per attribute count so that its per-particle arrays stay in registers).
+cudaError_t launch_bin_multi(const KernelCtx& kc, int dtype, const MultiSpec* dev_specs,
+                             const int* group_attrs, const int* group_size, int n_groups, int64_t n);
 
 // Shared-memory bytes the privatised kernel needs for this mesh, or 0 if
 // the mesh does not fit.

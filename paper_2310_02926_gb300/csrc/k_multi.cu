@@ -17,7 +17,38 @@
 
 namespace bn {
 
-template <typename T>
+// One spec over one tile. K: the spec's attribute count, so that the
+// per-particle values and the commit's partial sums live in registers (-1:
+// any count, through local memory).
+template <typename T, int K>
+__device__ __forceinline__ void multi_tile(const MultiSpec& sp, const Binner<T>& binner, int64_t i0,
+                                           int64_t i1) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = threadIdx.x & ~31;
+    const T* __restrict__ X = static_cast<const T*>(sp.x);
+    const T* __restrict__ Y = static_cast<const T*>(sp.y);
+    const int A = K >= 0 ? K : sp.n_attrs;
+    const bool agg = sp.aggregate != 0;
+    // whole warps iterate together (warp_commit needs every lane)
+    for (int64_t base = i0 + warp0; base < i1; base += blockDim.x) {
+        const int64_t i = base + lane;
+        int b = -1;
+        T v[K > 0 ? K : (K == 0 ? 1 : kMaxAttr)];
+        if (i < i1) {
+            b = binner.bin(X[i], Y[i]);
+            if constexpr (K > 0) {
+#pragma unroll
+                for (int a = 0; a < K; ++a) v[a] = static_cast<const T*>(sp.a[a])[i];
+            } else if constexpr (K < 0) {
+                for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(sp.a[a])[i];
+            }
+        }
+        warp_commit<T, K>(sp.st, A, b, v, agg);
+    }
+}
+
+// All specs of one launch have K attributes (the host groups them).
+template <typename T, int K>
 __global__ void __launch_bounds__(256) k_bin_multi(const MultiSpec* __restrict__ specs, int n_specs,
                                                    int64_t n) {
     // every spec's binner, built once per CTA
@@ -32,8 +63,6 @@ __global__ void __launch_bounds__(256) k_bin_multi(const MultiSpec* __restrict__
         binners[s] = bnr;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = threadIdx.x & ~31;
     const int64_t ntiles = (n + kMultiTile - 1) / kMultiTile;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int64_t i0 = t * kMultiTile;
@@ -51,40 +80,50 @@ __global__ void __launch_bounds__(256) k_bin_multi(const MultiSpec* __restrict__
                     dst[w] = src[w];
             }
             __syncthreads();
-            const MultiSpec& sp = cur;
-            const T* __restrict__ X = static_cast<const T*>(sp.x);
-            const T* __restrict__ Y = static_cast<const T*>(sp.y);
-            const int A = sp.n_attrs;
-            const bool agg = sp.aggregate != 0;
-            // whole warps iterate together (warp_commit needs every lane)
-            for (int64_t base = i0 + warp0; base < i1; base += blockDim.x) {
-                const int64_t i = base + lane;
-                int b = -1;
-                T v[kMaxAttr];
-                if (i < i1) {
-                    b = binner.bin(X[i], Y[i]);
-                    for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(sp.a[a])[i];
-                }
-                warp_commit<T, -1>(sp.st, A, b, v, agg);
-            }
+            multi_tile<T, K>(cur, binner, i0, i1);
         }
     }
 }
 
-cudaError_t launch_bin_multi(const KernelCtx& kc, int dtype, const MultiSpec* dev_specs, int n_specs,
-                             int64_t n) {
-    if (n <= 0 || n_specs <= 0) return cudaSuccess;
-    const int block = 256;
+template <typename T, int K>
+static void launch_group(const KernelCtx& kc, const MultiSpec* specs, int n_specs, int64_t n, int grid) {
+    k_bin_multi<T, K><<<grid, 256, sizeof(Binner<T>) * n_specs, kc.stream>>>(specs, n_specs, n);
+}
+
+template <typename T>
+static void launch_group_k(const KernelCtx& kc, int k, const MultiSpec* specs, int n_specs, int64_t n,
+                           int grid) {
+    switch (k) {
+        case 0: launch_group<T, 0>(kc, specs, n_specs, n, grid); break;
+        case 1: launch_group<T, 1>(kc, specs, n_specs, n, grid); break;
+        case 2: launch_group<T, 2>(kc, specs, n_specs, n, grid); break;
+        case 3: launch_group<T, 3>(kc, specs, n_specs, n, grid); break;
+        case 4: launch_group<T, 4>(kc, specs, n_specs, n, grid); break;
+        case 5: launch_group<T, 5>(kc, specs, n_specs, n, grid); break;
+        case 6: launch_group<T, 6>(kc, specs, n_specs, n, grid); break;
+        case 7: launch_group<T, 7>(kc, specs, n_specs, n, grid); break;
+        case 8: launch_group<T, 8>(kc, specs, n_specs, n, grid); break;
+        case 9: launch_group<T, 9>(kc, specs, n_specs, n, grid); break;
+        case 10: launch_group<T, 10>(kc, specs, n_specs, n, grid); break;
+        default: launch_group<T, -1>(kc, specs, n_specs, n, grid); break;
+    }
+}
+
+cudaError_t launch_bin_multi(const KernelCtx& kc, int dtype, const MultiSpec* dev_specs,
+                             const int* group_attrs, const int* group_size, int n_groups, int64_t n) {
+    if (n <= 0 || n_groups <= 0) return cudaSuccess;
     int64_t grid = (n + kMultiTile - 1) / kMultiTile;
     // 4 CTAs per SM: a tile's columns (kMultiTile x columns x 8 B) stay within
     // a CTA's share of L2 between the specs that read them
     const int64_t cap = (int64_t)kc.num_sms * 4;
     if (grid > cap) grid = cap;
-    if (dtype == BN_F64)
-        k_bin_multi<double><<<(int)grid, block, sizeof(Binner<double>) * n_specs, kc.stream>>>(dev_specs, n_specs, n);
-    else
-        k_bin_multi<float><<<(int)grid, block, sizeof(Binner<float>) * n_specs, kc.stream>>>(dev_specs, n_specs, n);
-    kc.count_launch();
+    const MultiSpec* p = dev_specs;
+    for (int g = 0; g < n_groups; ++g) {
+        if (dtype == BN_F64) launch_group_k<double>(kc, group_attrs[g], p, group_size[g], n, (int)grid);
+        else launch_group_k<float>(kc, group_attrs[g], p, group_size[g], n, (int)grid);
+        kc.count_launch();
+        p += group_size[g];
+    }
     return cudaGetLastError();
 }
 

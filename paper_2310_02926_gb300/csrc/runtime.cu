@@ -1057,16 +1057,28 @@ static bn_status enqueue_multi(bn_context* c, Plan& plan, const bn_buffer* cols,
         e = launch_init_state(kc, dtype, sd, nullptr);
         if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     }
-    // the descriptors; a pageable source is copied out before the call returns
+    // the descriptors, grouped by attribute count (one launch per group); a
+    // pageable source is copied out before the call returns
+    std::vector<MultiSpec> sorted(hs);
+    std::stable_sort(sorted.begin(), sorted.end(),
+                     [](const MultiSpec& a, const MultiSpec& b) { return a.n_attrs < b.n_attrs; });
+    std::vector<int> group_attrs, group_size;
+    for (const MultiSpec& m : sorted) {
+        if (group_attrs.empty() || group_attrs.back() != m.n_attrs) {
+            group_attrs.push_back(m.n_attrs);
+            group_size.push_back(0);
+        }
+        ++group_size.back();
+    }
     MultiSpec* ds = static_cast<MultiSpec*>(plan.alloc(sizeof(MultiSpec) * (size_t)n_specs));
     if (!ds) return cuda_fail(plan.err, "cudaMallocAsync(specs)");
-    cudaError_t e = cudaMemcpyAsync(ds, hs.data(), sizeof(MultiSpec) * (size_t)n_specs,
+    cudaError_t e = cudaMemcpyAsync(ds, sorted.data(), sizeof(MultiSpec) * (size_t)n_specs,
                                     cudaMemcpyHostToDevice, plan.stream);
     if (e != cudaSuccess) return cuda_fail(e, "copy specs");
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (c->profile && cudaEventCreate(&t0) == cudaSuccess && cudaEventCreate(&t1) == cudaSuccess)
         cudaEventRecord(t0, plan.stream);
-    e = launch_bin_multi(kc, dtype, ds, n_specs, n);
+    e = launch_bin_multi(kc, dtype, ds, group_attrs.data(), group_size.data(), (int)group_attrs.size(), n);
     if (t1) {
         cudaEventRecord(t1, plan.stream);
         std::lock_guard<std::mutex> lk(c->prof_mu);
