@@ -419,3 +419,4 @@ def test_shard_merge_keeps_both_compensation_terms():
     r = a.merge(b).finalize()
     assert r["sum"][0][0] == math.fsum([1e16, 1.0, -1e16, 1.0]) == 2.0
     assert r["count"][0] == 4
+
