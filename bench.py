@@ -71,6 +71,7 @@ KERNEL_SOURCES = {
     "global": ["paper_2310_02926_gb300/csrc/k_global.cu", "paper_2310_02926_gb300/csrc/bn_device.cuh"],
     "private": ["paper_2310_02926_gb300/csrc/k_private.cu", "paper_2310_02926_gb300/csrc/bn_device.cuh"],
     "sort": ["paper_2310_02926_gb300/csrc/k_sort.cu", "paper_2310_02926_gb300/csrc/bn_device.cuh"],
+    "hybrid": ["paper_2310_02926_gb300/csrc/k_window.cu", "paper_2310_02926_gb300/csrc/bn_device.cuh"],
 }
 COMMON_SOURCES = ["paper_2310_02926_gb300/csrc/bn_internal.cuh"]
 
@@ -300,7 +301,7 @@ def run_batch(args, n_blocks):
         gen_s = time.time() - t0
         ops = bn.OP_ALL | bn.SUM_F32C | {"auto": 0, "global": bn.STRATEGY_GLOBAL,
                                          "private": bn.STRATEGY_PRIVATE,
-                                         "sort": bn.STRATEGY_SORT}[args.strategy]
+                                         "sort": bn.STRATEGY_SORT, "hybrid": bn.STRATEGY_HYBRID}[args.strategy]
 
         def timed(fn, steps, warm):
             reqs = []
@@ -413,7 +414,7 @@ def run_multigrid(args, n):
             bn.bn_request_release(r)
 
         sep_ops = bn.OP_ALL | {"auto": 0, "global": bn.STRATEGY_GLOBAL, "private": bn.STRATEGY_PRIVATE,
-                               "sort": bn.STRATEGY_SORT}[args.strategy]
+                               "sort": bn.STRATEGY_SORT, "hybrid": bn.STRATEGY_HYBRID}[args.strategy]
 
         def separate():
             for (ia, ib, g, r, _) in sep:
@@ -600,7 +601,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-sample", type=int, default=2_000_000)
-    ap.add_argument("--strategy", default="auto", choices=["auto", "global", "private", "sort"])
+    ap.add_argument("--strategy", default="auto", choices=["auto", "global", "private", "sort", "hybrid"])
     ap.add_argument("--workload", default="plummer1024", choices=sorted(WORKLOADS))
     ap.add_argument("--n", type=int, default=0,
                     help="particles (0 = the workload's size; smaller cases for profiling runs)")
@@ -657,7 +658,7 @@ def main():
     cols = [torch.from_numpy(c).to(dev) for c in (w.x, w.y, *w.attrs)]
     ctx = bn.Context(local, stream=stream.cuda_stream, profile=True)
     flags = {"auto": 0, "global": bn.STRATEGY_GLOBAL, "private": bn.STRATEGY_PRIVATE,
-             "sort": bn.STRATEGY_SORT}[args.strategy]
+             "sort": bn.STRATEGY_SORT, "hybrid": bn.STRATEGY_HYBRID}[args.strategy]
     op_bits = {"all": bn.OP_ALL, "count": bn.OP_COUNT, "count+sum": bn.OP_COUNT | bn.OP_SUM,
                "count+minmax": bn.OP_COUNT | bn.OP_MIN | bn.OP_MAX}[args.ops]
     ops = op_bits | flags | {"f32c": bn.SUM_F32C, "f32": bn.SUM_F32, "f64": bn.SUM_F64}[args.sum]

@@ -174,6 +174,13 @@ enum {
     BN_STRATEGY_PRIVATE = 1u << 12, /* per-CTA shared-memory copy of the mesh */
     BN_STRATEGY_GLOBAL = 2u << 12,  /* warp-aggregated atomics into the global mesh */
     BN_STRATEGY_SORT = 3u << 12,    /* tile sort by bin + segmented reduce */
+    /* Global atomics with a shared-memory window: every CTA keeps the counts
+     * and sums of a rectangle of the densest bins in shared memory (sums as
+     * exact fixed-point integers) and merges them at the end; the rest of the
+     * mesh takes global atomics. The autotuner places the window on the
+     * counts of its trial pass; forced without a tuned placement, the window
+     * sits at the mesh centre. At most 4 attributes. */
+    BN_STRATEGY_HYBRID = 4u << 12,
     BN_STRATEGY_MASK = 15u << 12,
 
     /* Warp aggregation in the global-atomic strategy (bits 16-17): lanes of a
@@ -196,7 +203,10 @@ enum {
  *   sum[a], avg[a] f64 [bins]                     (BN_OP_SUM, BN_OP_AVG)
  *   min[a], max[a] T   [bins], T the data's dtype (BN_OP_MIN, BN_OP_MAX)
  *   bounds         f64 [4] = lo_x, hi_x, lo_y, hi_y actually used, in T
- *                  widened to f64 (optional; ptr NULL = not wanted)
+ *                  widened to f64 (optional; ptr NULL = not wanted); all
+ *                  four are quiet NaN when automatic bounds collapsed
+ *                  (BN_ERR_DEGENERATE), so a caller that does not read the
+ *                  request's status can still tell a failed call
  * Buffers for ops not requested are ignored.
  */
 typedef struct bn_result {
@@ -324,7 +334,12 @@ BN_API bn_status bn_bin_particles(bn_context* ctx, const bn_buffer* x, const bn_
  *   stream            all work is queued here (NULL = legacy default stream)
  *   sync              1: wait and return the device status (e.g.
  *                     BN_ERR_DEGENERATE); 0: return after queueing, device
- *                     errors are then not reported
+ *                     errors are then not reported. After an asynchronous
+ *                     call whose automatic bounds collapsed, the outputs
+ *                     hold the empty mesh (count 0, sum +0.0, min +inf, max
+ *                     -inf, avg NaN), the same as for input with no particle
+ *                     inside; give a bounds output to tell the two apart
+ *                     (it then holds four NaN)
  * Limit: f64 meshes need res_x + res_y <= 8062 (the edge keys must fit the
  * array); larger meshes are rejected with BN_ERR_INVALID_ARG. f32 meshes
  * have the usual limits.
@@ -343,8 +358,9 @@ BN_API bn_status bn_bin_particles_static(const bn_buffer* x, const bn_buffer* y,
  * in one persistent launch (the many binning operations per in situ step of
  * Sec. 4.3). Every block follows the rules of bn_bin_particles; all blocks
  * share one dtype, `ops` and n_attrs. The library chooses a strategy per
- * block (its autotuner) unless `ops` names one. Repeated batches with the
- * same block shapes replay a cached CUDA graph.
+ * block (its autotuner) unless `ops` names one (BN_STRATEGY_HYBRID blocks
+ * run the global strategy: batch blocks have no window). Repeated batches
+ * with the same block shapes replay a cached CUDA graph.
  */
 BN_API bn_status bn_bin_batch(bn_context* ctx, const bn_block* blocks, int n_blocks, uint32_t ops,
                        int sync, bn_request** req);

@@ -21,7 +21,7 @@ from ._abi import (CTX_PROFILE, ALLOC_CUDA_ASYNC, ALLOC_EXTERNAL, ALLOC_HOST, AL
                    ERR_INVALID_ARG, ERR_NO_MEMORY, ERR_TIMEOUT, F32, F64, HOST, MAX_ATTR,
                    MAX_BINS, MAX_RES, NOT_READY, OK, OP_ACCUMULATE, OP_ALL, OP_AVG, OP_COUNT,
                    OP_MAX, OP_MIN, OP_SUM, STRATEGY_AUTO, STRATEGY_GLOBAL, STRATEGY_MASK,
-                   STRATEGY_PRIVATE, STRATEGY_SORT, SUM_F32, SUM_F32C, SUM_F64, SUM_MASK, U64,
+                   STRATEGY_PRIVATE, STRATEGY_SORT, STRATEGY_HYBRID, SUM_F32, SUM_F32C, SUM_F64, SUM_MASK, U64,
                    AGG_AUTO, AGG_ON, AGG_OFF, AGG_MASK,
                    MAX_MULTI_COLS, MAX_MULTI_SPECS,
                    bn_block, bn_buffer, bn_grid, bn_grid_spec, bn_options, bn_result,
@@ -164,7 +164,8 @@ def bn_context_stream(ctx: int) -> int:
     return s.value or 0
 
 
-STRATEGY_NAMES = {STRATEGY_PRIVATE: "private", STRATEGY_GLOBAL: "global", STRATEGY_SORT: "sort"}
+STRATEGY_NAMES = {STRATEGY_PRIVATE: "private", STRATEGY_GLOBAL: "global", STRATEGY_SORT: "sort",
+                  STRATEGY_HYBRID: "hybrid"}
 
 
 def bn_context_profile(ctx: int):

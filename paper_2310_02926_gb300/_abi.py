@@ -45,6 +45,7 @@ STRATEGY_AUTO = 0 << 12
 STRATEGY_PRIVATE = 1 << 12
 STRATEGY_GLOBAL = 2 << 12
 STRATEGY_SORT = 3 << 12
+STRATEGY_HYBRID = 4 << 12
 STRATEGY_MASK = 15 << 12
 AGG_AUTO = 0 << 16
 AGG_ON = 1 << 16

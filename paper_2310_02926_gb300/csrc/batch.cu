@@ -412,7 +412,8 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
             SortDesc probe;
             ch.strategy = (f.bb.n > 0 && sort_plan(sort_args(f, dtype, A, sum_mode), c->smem_optin, &probe))
                               ? BN_STRATEGY_SORT : BN_STRATEGY_GLOBAL;
-        } else if (forced == BN_STRATEGY_GLOBAL) {
+        } else if (forced == BN_STRATEGY_GLOBAL || forced == BN_STRATEGY_HYBRID) {
+            // (batch blocks have no shared-memory window: a forced window runs global)
             ch.strategy = BN_STRATEGY_GLOBAL;
         } else {
             std::lock_guard<std::mutex> lk(cache.mu);

@@ -337,26 +337,91 @@ __device__ __forceinline__ void load_key_record(const int2* rec, int2* out, int 
     }
 }
 
+// Key pairs of a record / filter pairs of a filter record that a compile-time
+// attribute count needs in registers (kMaxAttr when the count is not fixed).
+template <typename K2, int A_CT>
+struct RecPairs {
+    static constexpr int Q = 32 / (int)sizeof(K2);
+    static constexpr int value = A_CT > 0 ? (A_CT + Q - 1) / Q * Q : kMaxAttr;
+};
+template <int A_CT>
+struct FltPairs {
+    static constexpr int value = A_CT > 0 ? (A_CT + 3) / 4 * 4 : kMaxAttr;
+};
+
+// Min and max of one particle (lo == hi == its values), or of a combined
+// group of particles (lo / hi: the group's min / max per attribute, +inf /
+// -inf where the group has no non-NaN value), into bin b's state. Three
+// forms of the state:
+//  - f64 key records behind the 32-bit filter (st.mmf): one 256-bit filter
+//    read per four attributes; only a key whose top half reaches the
+//    filter's bound updates the record, then lowers (raises) the filter;
+//  - key records alone (st.mmk): the record is read, an atomic is issued
+//    only where the key would change it;
+//  - the outputs themselves (raw IEEE bits, totalOrder atomics).
+template <typename T, int A_CT>
+__device__ __forceinline__ void commit_minmax(const StateDesc& st, int A, int64_t b, const T* lo,
+                                              const T* hi) {
+    if (!(st.do_min || st.do_max)) return;
+    using KO = KeyOf<T>;
+    using K2 = typename KO::K2;
+    if constexpr (sizeof(T) == 8) {
+        if (st.mmf) {
+            constexpr int FP = FltPairs<A_CT>::value;
+            int2 f[FP];
+            int2* fr = static_cast<int2*>(st.mmf) + b * filter_record_pairs(st.n_attrs);
+            load_key_record(fr, f, filter_record_pairs(A));
+            K2* kr = static_cast<K2*>(st.mmk) + b * key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
+            for (int a = 0; a < A; ++a) {
+                const long long kl = KO::key(lo[a]), kh = KO::key(hi[a]);
+                const int hl = (int)(kl >> 32), hh = (int)(kh >> 32);  // order preserving
+                if (st.do_min && hl <= f[a].x && !is_nan_bits(lo[a])) {
+                    atomicMin(&kr[a].x, kl);
+                    if (hl < f[a].x) atomicMin(&fr[a].x, hl);
+                }
+                if (st.do_max && hh >= f[a].y && !is_nan_bits(hi[a])) {
+                    atomicMax(&kr[a].y, kh);
+                    if (hh > f[a].y) atomicMax(&fr[a].y, hh);
+                }
+            }
+            return;
+        }
+    }
+    if (st.mmk) {
+        constexpr int RP = RecPairs<K2, A_CT>::value;
+        K2 rec[RP];
+        K2* kr = static_cast<K2*>(st.mmk) + b * key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
+        load_key_record(kr, rec, key_record_pairs(A, (int)sizeof(typename KO::K)));
+        for (int a = 0; a < A; ++a) {
+            if (st.do_min && !is_nan_bits(lo[a])) {
+                const auto kl = KO::key(lo[a]);
+                if (kl < rec[a].x) atomicMin(&kr[a].x, kl);
+            }
+            if (st.do_max && !is_nan_bits(hi[a])) {
+                const auto kh = KO::key(hi[a]);
+                if (kh > rec[a].y) atomicMax(&kr[a].y, kh);
+            }
+        }
+        return;
+    }
+    for (int a = 0; a < A; ++a) {
+        if (st.do_min && !is_nan_bits(lo[a])) {
+            T* g = static_cast<T*>(st.mn[a]) + b;
+            if (total_less(lo[a], filter_load(g))) atomic_min_total(g, lo[a]);
+        }
+        if (st.do_max && !is_nan_bits(hi[a])) {
+            T* g = static_cast<T*>(st.mx[a]) + b;
+            if (total_less(filter_load(g), hi[a])) atomic_max_total(g, hi[a]);
+        }
+    }
+}
+
 // Combine the lanes of the calling warp that share bin b (b >= 0) and let
 // the lowest such lane update the global mesh. Every lane of the warp must
 // call it (b = -1 for lanes without an in-bounds particle).
-// Shared-memory window of the global strategy: count and sums of the bins
-// [x0, x0 + nx) x [y0, y0 + ny) of a res_x-wide mesh, for one CTA.
-struct SmemWindow {
-    unsigned int* cnt;  // [nx * ny]
-    double* sum;        // [A][nx * ny]
-    int x0, y0, nx, ny, rx, W;
-    __device__ __forceinline__ int slot(int b) const {
-        if (nx == 0) return -1;
-        const int iy = b / rx, ix = b - iy * rx;
-        const int wx = ix - x0, wy = iy - y0;
-        return ((unsigned)wx < (unsigned)nx && (unsigned)wy < (unsigned)ny) ? wy * nx + wx : -1;
-    }
-};
-
 template <typename T, int A_CT>
 __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, const T* v,
-                                            bool aggregate, const SmemWindow* win = nullptr) {
+                                            bool aggregate) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned peers = aggregate ? __match_any_sync(full, b) : (1u << lane);
@@ -365,43 +430,10 @@ __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, c
     if (!aggregate || __all_sync(full, alone || b < 0)) {
         // no two lanes share a bin: skip the combining shuffles
         if (b < 0) return;
-        const int ws = win ? win->slot(b) : -1;
-        if (ws >= 0) atomicAdd(&win->cnt[ws], 1u);
-        else atomicAdd(&st.count[b], 1ull);
-        using KO = KeyOf<T>;
-        using K2 = typename KO::K2;
-        constexpr int RPC = A_CT > 0 ? (A_CT + 32 / (int)sizeof(K2) - 1) / (32 / (int)sizeof(K2)) * (32 / (int)sizeof(K2))
-                                     : kMaxAttr;
-        K2 rec[RPC];
-        K2* kr = nullptr;
-        if (st.mmk && (st.do_min || st.do_max)) {
-            // the bin's whole key record, 32 bytes per load
-            const int rp = key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
-            kr = static_cast<K2*>(st.mmk) + (int64_t)b * rp;
-            load_key_record(kr, rec, key_record_pairs(A, (int)sizeof(typename KO::K)));
-        }
-        for (int a = 0; a < A; ++a) {
-            const T x = v[a];
-            if (st.do_sum) {
-                if (ws >= 0) atomicAdd(&win->sum[a * win->W + ws], (double)x);
-                else atomicAdd(&st.sum[a][b], (double)x);
-            }
-            if (is_nan_bits(x)) continue;
-            if (kr) {
-                const auto key = KO::key(x);
-                if (st.do_min && key < rec[a].x) atomicMin(&kr[a].x, key);
-                if (st.do_max && key > rec[a].y) atomicMax(&kr[a].y, key);
-                continue;
-            }
-            if (st.do_min) {
-                T* g = static_cast<T*>(st.mn[a]) + b;
-                if (total_less(x, filter_load(g))) atomic_min_total(g, x);
-            }
-            if (st.do_max) {
-                T* g = static_cast<T*>(st.mx[a]) + b;
-                if (total_less(filter_load(g), x)) atomic_max_total(g, x);
-            }
-        }
+        atomicAdd(&st.count[b], 1ull);
+        if (st.do_sum)
+            for (int a = 0; a < A; ++a) atomicAdd(&st.sum[a][b], (double)v[a]);
+        commit_minmax<T, A_CT>(st, A, b, v, v);
         return;
     }
     // General case: the leader of each peer group gathers its peers' values
@@ -435,40 +467,12 @@ __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, c
         }
     }
     if (b < 0 || lane != leader) return;
-    const int ws = win ? win->slot(b) : -1;
-    if (ws >= 0) atomicAdd(&win->cnt[ws], cnt);
-    else atomicAdd(&st.count[b], (unsigned long long)cnt);
-    using KO = KeyOf<T>;
-    using K2 = typename KO::K2;
-    constexpr int RPC = A_CT > 0 ? (A_CT + 32 / (int)sizeof(K2) - 1) / (32 / (int)sizeof(K2)) * (32 / (int)sizeof(K2))
-                                 : kMaxAttr;
-    K2 rec[RPC];
-    K2* kr = nullptr;
-    if (st.mmk && (st.do_min || st.do_max)) {
-        const int rp = key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
-        kr = static_cast<K2*>(st.mmk) + (int64_t)b * rp;
-        load_key_record(kr, rec, key_record_pairs(A, (int)sizeof(typename KO::K)));
-    }
-    for (int a = 0; a < A; ++a) {
-        if (st.do_sum) {
-            if (ws >= 0) atomicAdd(&win->sum[a * win->W + ws], s[a]);
-            else atomicAdd(&st.sum[a][b], s[a]);
-        }
-        if (kr) {
-            const auto kl = KO::key(lo[a]), kh = KO::key(hi[a]);
-            if (st.do_min && kl < rec[a].x) atomicMin(&kr[a].x, kl);
-            if (st.do_max && kh > rec[a].y) atomicMax(&kr[a].y, kh);
-            continue;
-        }
-        if (st.do_min && !(lo[a] == pos_inf<T>())) {
-            T* g = static_cast<T*>(st.mn[a]) + b;
-            if (total_less(lo[a], filter_load(g))) atomic_min_total(g, lo[a]);
-        }
-        if (st.do_max && !(hi[a] == neg_inf<T>())) {
-            T* g = static_cast<T*>(st.mx[a]) + b;
-            if (total_less(filter_load(g), hi[a])) atomic_max_total(g, hi[a]);
-        }
-    }
+    atomicAdd(&st.count[b], (unsigned long long)cnt);
+    if (st.do_sum)
+        for (int a = 0; a < A; ++a) atomicAdd(&st.sum[a][b], s[a]);
+    // +inf / -inf where the group holds no non-NaN value: an atomic with them
+    // changes nothing, and the direct form skips them
+    commit_minmax<T, A_CT>(st, A, b, lo, hi);
 }
 
 }  // namespace bn

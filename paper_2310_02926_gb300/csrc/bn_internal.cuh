@@ -70,6 +70,13 @@ struct StateDesc {
     // and k_finalize writes mn/mx from them; when null, mn/mx hold the
     // running min/max directly.
     void* mmk;
+    // Optional filter in front of f64 key records (global strategy, three or
+    // more attributes): per bin filter_record_pairs(n_attrs) int2 pairs {top
+    // 32 bits of the min key, of the max key}, 32 bytes per four attributes,
+    // so one 256-bit load tells whether a particle can change any of the
+    // record's keys (a key whose top half is above the filter's min cannot
+    // lower the min). Only the keys that pass reach the records.
+    void* mmf;
     int64_t bins;
     int32_t n_attrs;
     int32_t do_sum;  // sums needed (SUM or AVG requested)
@@ -87,6 +94,11 @@ __host__ __device__ __forceinline__ int key_record_pairs(int n_attrs, int key_by
     if (n_attrs * pair <= 16) return 16 / pair;
     const int q = 32 / pair;
     return (n_attrs + q - 1) / q * q;
+}
+
+// int2 pairs per bin of StateDesc::mmf: whole 32-byte pieces of four pairs.
+__host__ __device__ __forceinline__ int filter_record_pairs(int n_attrs) {
+    return (n_attrs + 3) / 4 * 4;
 }
 
 // ---------------------------------------------------------------- bits

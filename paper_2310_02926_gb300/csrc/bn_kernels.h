@@ -44,7 +44,7 @@ struct BinArgs {
     int aggregate;          // global strategy: combine same-bin lanes of a warp first
     // global strategy: a window of bins whose count and sums each CTA keeps
     // in shared memory (win_nx == 0: none); bins [win_x0, win_x0 + win_nx) x
-    // [win_y0, win_y0 + win_ny)
+    // [win_y0, win_y0 + win_ny) (k_window.cu)
     int win_x0, win_y0, win_nx, win_ny;
     const void* x;
     const void* y;
@@ -131,7 +131,19 @@ cudaError_t launch_bin_multi(const KernelCtx& kc, int dtype, const MultiSpec* de
 // keys: -1 as a.st says; 0 / 1: f64 min/max without / with global key records.
 size_t private_smem_bytes(const BinArgs& a, int smem_optin, int keys = -1);
 cudaError_t launch_bin_private(const KernelCtx& kc, const BinArgs& a);
+// Global strategy; with a window (a.win_nx > 0) it runs launch_bin_window.
 cudaError_t launch_bin_global(const KernelCtx& kc, const BinArgs& a);
-size_t global_window_bytes(int win_cells, int n_attrs, bool do_sum);
+
+// Global strategy with a shared-memory window of win_nx x win_ny bins whose
+// counts and sums (96-bit fixed point) each CTA keeps privately (k_window.cu).
+constexpr int kWindowMaxAttr = 4;
+cudaError_t launch_bin_window(const KernelCtx& kc, const BinArgs& a);
+// Shared-memory bytes of a window of `cells` bins.
+size_t window_bytes(int cells, int n_attrs, bool do_sum);
+
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum (less its static shared memory), once per kernel and device;
+// safe to call from several threads.
+cudaError_t raise_smem_limit(const void* kernel, int smem_optin);
 
 }  // namespace bn

@@ -209,19 +209,11 @@ template <typename T, int A_CT, int MODE>
 static cudaError_t launch_batch_bin_t(const KernelCtx& kc, const BatchBlock* blocks, const int4* items,
                                       int n_items, int* counter, int n_attrs, size_t smem) {
     auto kern = k_batch_bin<T, A_CT, MODE>;
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, kern);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kc.smem_optin - (int)fa.sharedSizeBytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(kern), kc.smem_optin);
+    if (e != cudaSuccess) return e;
     const int block = 1024;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = kc.num_sms * per_sm;

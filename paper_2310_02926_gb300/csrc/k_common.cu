@@ -5,13 +5,38 @@
 //   merge of partial results of one mesh, and a strided-column gather.
 #include <cuda_runtime.h>
 
+#include <climits>
+#include <mutex>
+#include <set>
 #include <type_traits>
+#include <utility>
 
 #include "bn_device.cuh"
 #include "bn_internal.cuh"
 #include "bn_kernels.h"
 
 namespace bn {
+
+// ------------------------------------------------------------------ launch set-up
+// cudaFuncSetAttribute acts on the current device's context, so the limit is
+// raised once per (kernel, device); the server's worker thread and caller
+// threads launch concurrently, hence the lock.
+cudaError_t raise_smem_limit(const void* kernel, int smem_optin) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({kernel, dev})) return cudaSuccess;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done.insert({kernel, dev});
+    return e;
+}
 
 // ------------------------------------------------------------------ init
 // Empty-bin state: count 0, sum +0.0, min +inf, max -inf.
@@ -35,6 +60,11 @@ __global__ void k_init_state(StateDesc st, T* bounds_acc) {
         const int64_t pairs = B * key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
         auto* kp = static_cast<typename KO::K2*>(st.mmk);
         for (int64_t q = t0; q < pairs; q += stride) kp[q] = init;
+    }
+    if (st.mmf) {
+        const int64_t pairs = B * filter_record_pairs(st.n_attrs);
+        int2* fp = static_cast<int2*>(st.mmf);
+        for (int64_t q = t0; q < pairs; q += stride) fp[q] = make_int2(INT_MAX, INT_MIN);
     }
     for (int a = 0; a < st.n_attrs; ++a) {
         if (st.do_sum)
@@ -182,6 +212,11 @@ __global__ void k_grid_setup(GridDesc host_desc, const T* bounds_acc, GridDesc* 
                 bounds_out[1] = g.ax[0].hi;
                 bounds_out[2] = g.ax[1].lo;
                 bounds_out[3] = g.ax[1].hi;
+            } else if (bounds_out) {
+                // collapsed automatic bounds: NaN marks the result as failed
+                // for callers that do not read the request's status
+                const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+                for (int k = 0; k < 4; ++k) bounds_out[k] = qnan;
             }
         }
     }

@@ -9,6 +9,7 @@
 // only let through an atomic that turns out to be unnecessary). Lanes of a
 // warp that hit the same bin are combined first (__match_any_sync) so a
 // cluster of particles costs one set of atomics per warp, not per lane.
+// With a window (BinArgs::win_*), k_window.cu's kernel runs instead.
 #include <cuda_runtime.h>
 
 #include "bn_device.cuh"
@@ -60,12 +61,10 @@ template <> struct GBinner<double> {
     }
 };
 
-// NT threads per CTA: 256 without a window; with a shared-memory window one
-// CTA fills an SM's shared memory, so it runs 1024 threads (at most 64
-// registers) to keep 32 warps per SM.
+// 256 threads per CTA (77 registers at three f64 attributes: three CTAs
+// per SM; capping at 64 registers for four was measured slower).
 template <typename T, int A_CT, int NT>
 __global__ void __launch_bounds__(NT) k_bin_global(BinArgs args, int64_t head, int64_t groups) {
-    extern __shared__ __align__(16) unsigned char wsmem[];
     using V = typename GVec<T>::type;
     constexpr int VN = GVec<T>::N;
     constexpr int AC = A_CT > 0 ? A_CT : kMaxAttr;
@@ -82,25 +81,6 @@ __global__ void __launch_bounds__(NT) k_bin_global(BinArgs args, int64_t head, i
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 
-    // optional shared-memory window (count and sums of the densest bins)
-    SmemWindow wv;
-    const SmemWindow* win = nullptr;
-    if (args.win_nx > 0) {
-        wv.x0 = args.win_x0;
-        wv.y0 = args.win_y0;
-        wv.nx = args.win_nx;
-        wv.ny = args.win_ny;
-        wv.rx = g.ax[0].res;
-        wv.W = args.win_nx * args.win_ny;
-        wv.cnt = reinterpret_cast<unsigned int*>(wsmem);
-        wv.sum = reinterpret_cast<double*>(wsmem + (((size_t)wv.W * 4 + 15) & ~(size_t)15));
-        for (int k = threadIdx.x; k < wv.W; k += blockDim.x) wv.cnt[k] = 0u;
-        if (st.do_sum)
-            for (int k = threadIdx.x; k < A * wv.W; k += blockDim.x) wv.sum[k] = 0.0;
-        __syncthreads();
-        win = &wv;
-    }
-
     // scalar head and tail: whole warps iterate together (warp_commit needs
     // every lane), lanes past the end pass b = -1
     const int64_t tail0 = head + groups * VN;
@@ -114,7 +94,7 @@ __global__ void __launch_bounds__(NT) k_bin_global(BinArgs args, int64_t head, i
                 b = binner.bin(X[i], Y[i]);
                 for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(args.a[a])[i];
             }
-            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0, win);
+            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0);
         }
     };
     scalar_range(0, head);
@@ -150,20 +130,7 @@ __global__ void __launch_bounds__(NT) k_bin_global(BinArgs args, int64_t head, i
                     for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(args.a[a])[i];
                 }
             }
-            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0, win);
-        }
-    }
-    if (win) {
-        // this CTA's window partials into the global mesh
-        __syncthreads();
-        for (int k = threadIdx.x; k < wv.W; k += blockDim.x) {
-            const unsigned int c = wv.cnt[k];
-            if (!c) continue;
-            const int wy = k / wv.nx, wx = k - wy * wv.nx;
-            const int64_t b = (int64_t)(wv.y0 + wy) * wv.rx + (wv.x0 + wx);
-            atomicAdd(&st.count[b], (unsigned long long)c);
-            if (st.do_sum)
-                for (int a = 0; a < A; ++a) atomicAdd(&st.sum[a][b], wv.sum[a * wv.W + k]);
+            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0);
         }
     }
 }
@@ -187,49 +154,17 @@ static void gvector_split(const BinArgs& a, int64_t* head, int64_t* groups) {
     *groups = (a.n - h) / VN;
 }
 
-size_t global_window_bytes(int win_cells, int n_attrs, bool do_sum) {
-    if (win_cells <= 0) return 0;
-    return (((size_t)win_cells * 4 + 15) & ~(size_t)15) + (do_sum ? (size_t)n_attrs * win_cells * 8 : 0);
-}
-
 template <typename T, int A_CT>
 static cudaError_t launch_global_t(const KernelCtx& kc, const BinArgs& a) {
     int64_t head, groups;
     gvector_split<T>(a, &head, &groups);
     const int64_t work = groups > 0 ? groups : a.n;
-    if (a.win_nx <= 0) {
-        const int block = 256;
-        int64_t grid = (work + block - 1) / block;
-        const int64_t cap = (int64_t)kc.num_sms * 8;
-        if (grid > cap) grid = cap;
-        if (grid < 1) grid = 1;
-        k_bin_global<T, A_CT, 256><<<(int)grid, block, 0, kc.stream>>>(a, head, groups);
-        kc.count_launch();
-        return cudaGetLastError();
-    }
-    // one window copy per CTA: as many 1024-thread CTAs as fit, all resident
-    const int block = 1024;
-    auto kern = k_bin_global<T, A_CT, 1024>;
-    const size_t smem = global_window_bytes(a.win_nx * a.win_ny, a.n_attrs, a.st.do_sum != 0);
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, kern);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kc.smem_optin - (int)fa.sharedSizeBytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int block = 256;
     int64_t grid = (work + block - 1) / block;
-    const int64_t cap = (int64_t)kc.num_sms * per_sm;
+    const int64_t cap = (int64_t)kc.num_sms * 8;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    kern<<<(int)grid, block, smem, kc.stream>>>(a, head, groups);
+    k_bin_global<T, A_CT, 256><<<(int)grid, block, 0, kc.stream>>>(a, head, groups);
     kc.count_launch();
     return cudaGetLastError();
 }
@@ -247,6 +182,7 @@ static cudaError_t dispatch_global(const KernelCtx& kc, const BinArgs& a) {
 }
 
 cudaError_t launch_bin_global(const KernelCtx& kc, const BinArgs& a) {
+    if (a.win_nx > 0 && a.win_ny > 0) return launch_bin_window(kc, a);
     return a.dtype == BN_F64 ? dispatch_global<double>(kc, a) : dispatch_global<float>(kc, a);
 }
 

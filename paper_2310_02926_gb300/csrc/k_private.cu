@@ -185,13 +185,8 @@ size_t private_smem_bytes(const BinArgs& a, int smem_optin, int keys) {
 template <typename T, int A_CT, int MODE, int NT>
 static cudaError_t configure_private(const KernelCtx& kc, size_t smem, int* per_sm) {
     auto kern = k_bin_private<T, A_CT, MODE, NT>;
-    static bool configured = false;  // per instantiation
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kc.smem_optin);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(kern), kc.smem_optin);
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, NT, smem);
 }
 

@@ -406,22 +406,10 @@ static cudaError_t launch_sort_t(const KernelCtx& kc, const BinArgs& a, const So
     auto scat = sd.per == 16 ? k_sort_scatter<T, A_CT, 16> : k_sort_scatter<T, A_CT, 8>;
     auto red = k_sort_reduce<T, A_CT, MODE>;
     auto cnt = k_sort_count<T>;
-    static bool configured[2] = {false, false};
-    const int ci = sd.per == 16 ? 1 : 0;
-    if (!configured[ci]) {
-        // the opt-in limit covers static plus dynamic shared memory
-        cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, scat);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(scat, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kc.smem_optin - (int)fa.sharedSizeBytes);
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, red);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(red, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kc.smem_optin - (int)fa.sharedSizeBytes);
-        if (e != cudaSuccess) return e;
-        configured[ci] = true;
-    }
+    // the opt-in limit covers static plus dynamic shared memory
+    cudaError_t e0 = raise_smem_limit(reinterpret_cast<const void*>(scat), kc.smem_optin);
+    if (e0 == cudaSuccess) e0 = raise_smem_limit(reinterpret_cast<const void*>(red), kc.smem_optin);
+    if (e0 != cudaSuccess) return e0;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cnt, 512, sd.smem_count);
     if (e != cudaSuccess) return e;

@@ -1,0 +1,373 @@
+// k_window.cu -- the global-atomic strategy with a privatised window: each
+// CTA keeps the count and the sums of a rectangle of the densest bins in
+// shared memory, the rest of the mesh takes global atomics as in
+// k_global.cu (Sec. 4.2 binning; Sec. 4.4 names the atomic updates as its
+// GPU cost, and a centrally concentrated body set piles most particles
+// into few bins).
+//
+// Shared-memory sums are fixed-point integers, not FP64: GB300's FP64 pipe
+// is narrow, and an FP64 add to shared memory is a compare-and-swap loop
+// (measured 145 G adds/s over the GPU, against 475 G/s for 64-bit integer
+// adds and 1520 G/s for 32-bit ones). Each CTA picks, per attribute, a scale
+// 2^F from the largest exponent among the first values it reads. A value v
+// whose magnitude lies in a 17-binade range below that maximum becomes the
+// integer q = trunc(v * 2^F), |q| < 2^62, losing at most 2^-45 of |v|
+// (f32 values are converted exactly); q is added to a 96-bit accumulator
+// (a u64 low word with a 64-bit integer atomic, and a 32-bit high word that
+// takes the rare carry or borrow). Integer addition is exact and
+// associative, so a window sum is exact up to those conversion losses,
+// whatever the order. Values outside the range (and NaN, +-inf,
+// subnormals) go to the FP64 atomic in global memory like every particle
+// outside the window. At the end each CTA converts its window sums to FP64
+// and merges them, with its counts, into the global mesh.
+//
+// Per-bin error of a window sum: at most 2^-45 * sum|a| from the
+// conversions, plus one rounding of the converted partial and the FP64
+// merge adds: well inside the 1e-12 * sum|a| contract of the FP64 path.
+//
+// Min and max are not privatised: every particle goes through
+// commit_minmax (key records, with the 32-bit filter for f64 data).
+#include <cuda_runtime.h>
+
+#include "bn_device.cuh"
+#include "bn_internal.cuh"
+#include "bn_kernels.h"
+
+namespace bn {
+
+// ---------------------------------------------------------------- fixed point
+template <typename T> struct Fixed;
+
+template <> struct Fixed<double> {
+    static constexpr int kExpMax = 0x7ff;  // inf / NaN
+    static constexpr int kDefault = 1023;  // the exponent of 1.0
+    static __device__ __forceinline__ int expo(double v) {
+        return (int)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff;
+    }
+    // The largest sampled biased exponent emax is given two binades of
+    // headroom: |v| < 2^(emax - 1021) maps below 2^62.
+    static __device__ __forceinline__ int scale(int emax) {
+        if (emax <= 0 || emax >= kExpMax) emax = kDefault;
+        return 9 + 1075 - (emax + 2);
+    }
+    // v = +-m * 2^(e - 1075), m the 53-bit significand; q = +-m * 2^sh with
+    // sh = e - 1075 + F. Accepted for -7 <= sh <= 9: |q| < 2^62, and at most
+    // 7 of m's 53 bits are dropped (relative loss < 2^-45). Zero is q = 0.
+    static __device__ __forceinline__ bool to_fixed(double v, int F, long long* q) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        const int e = (int)(b >> 52) & 0x7ff;
+        if (e == 0) {
+            *q = 0;
+            return (b << 1) == 0ull;  // +-0 accepted, subnormals not
+        }
+        const int sh = e - 1075 + F;
+        if (e == kExpMax || sh > 9 || sh < -7) return false;
+        const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+        const unsigned long long mag = sh >= 0 ? (m << sh) : (m >> (-sh));
+        *q = (b >> 63) ? -(long long)mag : (long long)mag;
+        return true;
+    }
+};
+
+template <> struct Fixed<float> {
+    static constexpr int kExpMax = 0xff;
+    static constexpr int kDefault = 127;
+    static __device__ __forceinline__ int expo(float v) { return (int)(__float_as_uint(v) >> 23) & 0xff; }
+    static __device__ __forceinline__ int scale(int emax) {
+        if (emax <= 0 || emax >= kExpMax) emax = kDefault;
+        return 38 + 150 - (emax + 2);
+    }
+    // v = +-m * 2^(e - 150), m the 24-bit significand; exact for
+    // 0 <= sh = e - 150 + F <= 38 (|q| < 2^62).
+    static __device__ __forceinline__ bool to_fixed(float v, int F, long long* q) {
+        const unsigned b = __float_as_uint(v);
+        const int e = (int)(b >> 23) & 0xff;
+        if (e == 0) {
+            *q = 0;
+            return (b << 1) == 0u;
+        }
+        const int sh = e - 150 + F;
+        if (e == kExpMax || sh > 38 || sh < 0) return false;
+        const unsigned long long mag = (unsigned long long)((b & 0x7fffffu) | 0x800000u) << sh;
+        *q = (b >> 31) ? -(long long)mag : (long long)mag;
+        return true;
+    }
+};
+
+// 2^k for -1022 <= k <= 1023, from its bits.
+__device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+
+// The signed 96-bit value hi * 2^64 + lo, times 2^-F, as FP64. The scaling
+// is two multiplications by powers of two (each factor a normal double for
+// |F| <= 2044), exact unless the result falls below the normal range.
+__device__ __forceinline__ double fixed_value(unsigned long long lo, int hi, int F) {
+    double d;
+    if ((hi == 0 && (long long)lo >= 0) || (hi == -1 && (long long)lo < 0))
+        d = __ll2double_rn((long long)lo);  // fits in 64 bits: one rounding
+    else
+        d = __dadd_rn(__dmul_rn((double)hi, 18446744073709551616.0), __ull2double_rn(lo));
+    const int f1 = F / 2;
+    return __dmul_rn(__dmul_rn(d, pow2(-f1)), pow2(f1 - F));
+}
+
+// ---------------------------------------------------------------- window
+size_t window_bytes(int cells, int n_attrs, bool do_sum) {
+    if (cells <= 0) return 0;
+    return (((size_t)cells * 4 + 15) & ~(size_t)15) + (do_sum ? (size_t)n_attrs * cells * 12 : 0);
+}
+
+template <typename T> struct WinAxes;
+template <> struct WinAxes<float> {
+    Axis<float> ax, ay;
+    __device__ void init(const GridDesc& g) {
+        ax = make_axis<float>(g.ax[0]);
+        ay = make_axis<float>(g.ax[1]);
+    }
+    __device__ __forceinline__ int bx(float x) const { return axis_bin(ax, x); }
+    __device__ __forceinline__ int by(float y) const { return axis_bin(ay, y); }
+};
+template <> struct WinAxes<double> {
+    AxisF64 ax, ay;
+    __device__ void init(const GridDesc& g) {
+        ax = make_axis_f64(g.ax[0], g.edges[0]);
+        ay = make_axis_f64(g.ax[1], g.edges[1]);
+    }
+    __device__ __forceinline__ int bx(double x) const { return axis_bin(ax, x); }
+    __device__ __forceinline__ int by(double y) const { return axis_bin(ay, y); }
+};
+
+template <typename T, int A_CT, int NT>
+__global__ void __launch_bounds__(NT, 1) k_bin_window(BinArgs args, int64_t head, int64_t groups) {
+    extern __shared__ __align__(16) unsigned char wsm[];
+    __shared__ int s_emax[kMaxAttr];
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::N;
+    constexpr int A = A_CT;
+    constexpr int AC = A > 0 ? A : 1;
+    const GridDesc g = args.dev_grid ? *args.dev_grid : args.grid;
+    if (!g.valid) return;
+    const StateDesc& st = args.st;
+    const bool do_sum = st.do_sum != 0;
+    WinAxes<T> axes;
+    axes.init(g);
+    const int rx = g.ax[0].res;
+    const int x0 = args.win_x0, y0 = args.win_y0, nx = args.win_nx, ny = args.win_ny;
+    const int W = nx * ny;
+    unsigned int* cnt = reinterpret_cast<unsigned int*>(wsm);
+    unsigned long long* lo = reinterpret_cast<unsigned long long*>(wsm + (((size_t)W * 4 + 15) & ~(size_t)15));
+    int* hi = reinterpret_cast<int*>(lo + (size_t)A * W);
+
+    for (int k = threadIdx.x; k < W; k += NT) cnt[k] = 0u;
+    if (do_sum) {
+        for (int k = threadIdx.x; k < A * W; k += NT) {
+            lo[k] = 0ull;
+            hi[k] = 0;
+        }
+    }
+    if (threadIdx.x < kMaxAttr) s_emax[threadIdx.x] = 0;
+    __syncthreads();
+
+    const T* __restrict__ X = static_cast<const T*>(args.x);
+    const T* __restrict__ Y = static_cast<const T*>(args.y);
+    const T* __restrict__ AT[AC];
+#pragma unroll
+    for (int a = 0; a < AC; ++a) AT[a] = A > 0 ? static_cast<const T*>(args.a[a]) : nullptr;
+    const int64_t n = args.n;
+    const int64_t nthreads = (int64_t)gridDim.x * NT;
+    const int64_t tid = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const V* __restrict__ XV = reinterpret_cast<const V*>(X + head);
+    const V* __restrict__ YV = reinterpret_cast<const V*>(Y + head);
+
+    // Scale per attribute: the largest finite exponent among this CTA's
+    // first values (each thread's first vector group, or first particle).
+    int F[AC];
+    if (A > 0 && do_sum) {
+        int em[AC];
+#pragma unroll
+        for (int a = 0; a < AC; ++a) em[a] = 0;
+        auto see = [&](int a, T v) {
+            const int e = Fixed<T>::expo(v);
+            if (e < Fixed<T>::kExpMax) em[a] = max(em[a], e);
+        };
+        if (groups > 0) {
+            if (tid < groups)
+#pragma unroll
+                for (int a = 0; a < AC; ++a) {
+                    const V v = __ldg(reinterpret_cast<const V*>(AT[a] + head) + tid);
+#pragma unroll
+                    for (int j = 0; j < VN; ++j) see(a, vget<T>(v, j));
+                }
+        } else if (tid < n) {
+#pragma unroll
+            for (int a = 0; a < AC; ++a) see(a, AT[a][tid]);
+        }
+#pragma unroll
+        for (int a = 0; a < AC; ++a) {
+            for (int off = 16; off > 0; off >>= 1) em[a] = max(em[a], __shfl_xor_sync(0xffffffffu, em[a], off));
+            if ((threadIdx.x & 31) == 0) atomicMax(&s_emax[a], em[a]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < AC; ++a) F[a] = Fixed<T>::scale(s_emax[a]);
+    } else {
+#pragma unroll
+        for (int a = 0; a < AC; ++a) F[a] = 0;
+    }
+
+    auto one = [&](T x, T y, const T* v) {
+        const int ix = axes.bx(x);
+        const int iy = axes.by(y);
+        if (ix < 0 || iy < 0) return;
+        const int64_t b = (int64_t)iy * rx + ix;
+        const unsigned wx = (unsigned)(ix - x0), wy = (unsigned)(iy - y0);
+        if (wx < (unsigned)nx && wy < (unsigned)ny) {
+            const int k = (int)wy * nx + (int)wx;
+            atomicAdd(&cnt[k], 1u);
+            if (do_sum) {
+#pragma unroll
+                for (int a = 0; a < A; ++a) {
+                    long long q;
+                    if (Fixed<T>::to_fixed(v[a], F[a], &q)) {
+                        if (q == 0) continue;
+                        // 96-bit add: carry out of the low word (q >= 0), or
+                        // no borrow-free wrap (q < 0), moves the high word
+                        const unsigned long long u = (unsigned long long)q;
+                        const unsigned long long old = atomicAdd(&lo[a * W + k], u);
+                        const bool carry = old + u < old;
+                        const int d = q >= 0 ? (carry ? 1 : 0) : (carry ? 0 : -1);
+                        if (d) atomicAdd(&hi[a * W + k], d);
+                    } else {
+                        atomicAdd(&st.sum[a][b], (double)v[a]);
+                    }
+                }
+            }
+        } else {
+            atomicAdd(&st.count[b], 1ull);
+            if (do_sum)
+#pragma unroll
+                for (int a = 0; a < A; ++a) atomicAdd(&st.sum[a][b], (double)v[a]);
+        }
+        if (A > 0) commit_minmax<T, A>(st, A, b, v, v);
+    };
+
+    // scalar head and tail
+    for (int64_t i = tid; i < head; i += nthreads) {
+        T v[AC];
+#pragma unroll
+        for (int a = 0; a < A; ++a) v[a] = AT[a][i];
+        one(X[i], Y[i], v);
+    }
+    for (int64_t i = head + groups * VN + tid; i < n; i += nthreads) {
+        T v[AC];
+#pragma unroll
+        for (int a = 0; a < A; ++a) v[a] = AT[a][i];
+        one(X[i], Y[i], v);
+    }
+    // vector groups, two per thread and iteration so that more loads are in
+    // flight while the atomics of the previous ones drain
+    for (int64_t gi = tid; gi < groups; gi += 2 * nthreads) {
+        const int64_t g2 = gi + nthreads;
+        const bool live2 = g2 < groups;
+        V xv[2], yv[2], av[2][AC];
+        xv[0] = __ldcs(XV + gi);
+        yv[0] = __ldcs(YV + gi);
+#pragma unroll
+        for (int a = 0; a < A; ++a) av[0][a] = __ldcs(reinterpret_cast<const V*>(AT[a] + head) + gi);
+        if (live2) {
+            xv[1] = __ldcs(XV + g2);
+            yv[1] = __ldcs(YV + g2);
+#pragma unroll
+            for (int a = 0; a < A; ++a) av[1][a] = __ldcs(reinterpret_cast<const V*>(AT[a] + head) + g2);
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (r == 1 && !live2) break;
+#pragma unroll
+            for (int j = 0; j < VN; ++j) {
+                T v[AC];
+#pragma unroll
+                for (int a = 0; a < A; ++a) v[a] = vget<T>(av[r][a], j);
+                one(vget<T>(xv[r], j), vget<T>(yv[r], j), v);
+            }
+        }
+    }
+
+    // this CTA's window into the global mesh
+    __syncthreads();
+    for (int k = threadIdx.x; k < W; k += NT) {
+        const unsigned int c = cnt[k];
+        if (!c) continue;
+        const int wy = k / nx, wx = k - wy * nx;
+        const int64_t b = (int64_t)(y0 + wy) * rx + (x0 + wx);
+        atomicAdd(&st.count[b], (unsigned long long)c);
+        if (do_sum)
+#pragma unroll
+            for (int a = 0; a < A; ++a) {
+                const unsigned long long l = lo[a * W + k];
+                const int h = hi[a * W + k];
+                if (l != 0ull || h != 0) atomicAdd(&st.sum[a][b], fixed_value(l, h, F[a]));
+            }
+    }
+}
+
+template <typename T>
+static void window_split(const BinArgs& a, int64_t* head, int64_t* groups) {
+    constexpr int VN = VecOf<T>::N;
+    auto phase = [](const void* p) { return (int)(((uintptr_t)p / sizeof(T)) % VN); };
+    const int ph = phase(a.x);
+    bool same = phase(a.y) == ph;
+    for (int k = 0; k < a.n_attrs; ++k) same = same && phase(a.a[k]) == ph;
+    if (!same) {
+        *head = a.n;
+        *groups = 0;
+        return;
+    }
+    int64_t h = (VN - ph) % VN;
+    if (h > a.n) h = a.n;
+    *head = h;
+    *groups = (a.n - h) / VN;
+}
+
+template <typename T, int A_CT>
+static cudaError_t launch_window_t(const KernelCtx& kc, const BinArgs& a) {
+    constexpr int NT = 512;
+    auto kern = k_bin_window<T, A_CT, NT>;
+    const size_t smem = window_bytes(a.win_nx * a.win_ny, a.n_attrs, a.st.do_sum != 0);
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(kern), kc.smem_optin);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int64_t head, groups;
+    window_split<T>(a, &head, &groups);
+    const int64_t work = groups > 0 ? groups : a.n;
+    int64_t grid = (work + NT - 1) / NT;
+    const int64_t cap = (int64_t)kc.num_sms * per_sm;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    kern<<<(int)grid, NT, smem, kc.stream>>>(a, head, groups);
+    kc.count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t dispatch_window(const KernelCtx& kc, const BinArgs& a) {
+    switch (a.n_attrs) {
+        case 0: return launch_window_t<T, 0>(kc, a);
+        case 1: return launch_window_t<T, 1>(kc, a);
+        case 2: return launch_window_t<T, 2>(kc, a);
+        case 3: return launch_window_t<T, 3>(kc, a);
+        case 4: return launch_window_t<T, 4>(kc, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_bin_window(const KernelCtx& kc, const BinArgs& a) {
+    if (a.n_attrs > kWindowMaxAttr || a.win_nx <= 0 || a.win_ny <= 0) return cudaErrorInvalidValue;
+    const size_t smem = window_bytes(a.win_nx * a.win_ny, a.n_attrs, a.st.do_sum != 0);
+    if (smem > (size_t)kc.smem_optin - 1024) return cudaErrorInvalidValue;
+    return a.dtype == BN_F64 ? dispatch_window<double>(kc, a) : dispatch_window<float>(kc, a);
+}
+
+}  // namespace bn

@@ -537,11 +537,25 @@ bn_status Plan::finish(bn_request* r) {
 }
 
 // ------------------------------------------------------------------ binning
+// The largest window of a res_x x res_y mesh whose counts and sums fit one
+// CTA's shared memory (k_window.cu), about square; false if none fits or
+// the attribute count has no window kernel.
+static bool window_shape(int rx, int ry, int n_attrs, bool do_sum, int smem_optin, int* wnx, int* wny) {
+    if (n_attrs > kWindowMaxAttr) return false;
+    int cells = 0;
+    while (window_bytes(cells + 64, n_attrs, do_sum) <= (size_t)(smem_optin - 1024)) cells += 64;
+    const int side = (int)std::sqrt((double)cells);
+    *wnx = std::min(side, rx);
+    *wny = std::min(cells / std::max(*wnx, 1), ry);
+    return *wnx >= 1 && *wny >= 1;
+}
+
 int bn::choose_strategy(const BinArgs& a, int smem_optin, int num_sms, uint32_t ops) {
     const uint32_t forced = ops & BN_STRATEGY_MASK;
     if (forced == BN_STRATEGY_PRIVATE) return BN_STRATEGY_PRIVATE;
     if (forced == BN_STRATEGY_GLOBAL) return BN_STRATEGY_GLOBAL;
     if (forced == BN_STRATEGY_SORT) return BN_STRATEGY_SORT;
+    if (forced == BN_STRATEGY_HYBRID) return BN_STRATEGY_HYBRID;
     const size_t smem = private_smem_bytes(a, smem_optin);
     const int64_t B = (int64_t)a.grid.ax[0].res * a.grid.ax[1].res;
     // Privatise when the mesh fits and there are enough particles per CTA
@@ -576,7 +590,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
     if (st == BN_OK) st = validate_buffer(c, y, n, dtype, "y");
     for (int a = 0; a < n_attrs && st == BN_OK; ++a) st = validate_buffer(c, &attrs[a], n, dtype, "attr");
     if (st != BN_OK) return st;
-    if ((ops & BN_STRATEGY_MASK) > BN_STRATEGY_SORT)
+    if ((ops & BN_STRATEGY_MASK) > BN_STRATEGY_HYBRID)
         return fail(BN_ERR_INVALID_ARG, "unknown strategy in ops");
     if ((ops & BN_AGG_MASK) == BN_AGG_MASK) return fail(BN_ERR_INVALID_ARG, "unknown aggregation mode in ops");
     const uint32_t sum_bits = ops & BN_SUM_MASK;
@@ -691,24 +705,43 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
                 if (!aggbits) args.aggregate = it->second.aggregate;
                 if (strat == BN_STRATEGY_GLOBAL && it->second.win_nx > 0 &&
                     it->second.win_x0 + it->second.win_nx <= grid->res[0] &&
-                    it->second.win_y0 + it->second.win_ny <= grid->res[1]) {
+                    it->second.win_y0 + it->second.win_ny <= grid->res[1] &&
+                    window_bytes(it->second.win_nx * it->second.win_ny, n_attrs, sd.do_sum != 0) <=
+                        (size_t)(c->smem_optin - 1024)) {
                     args.win_x0 = it->second.win_x0;
                     args.win_y0 = it->second.win_y0;
                     args.win_nx = it->second.win_nx;
                     args.win_ny = it->second.win_ny;
+                    strat = BN_STRATEGY_HYBRID;
                 }
             } else if (n >= (int64_t)1 << 16 && !accumulate && plan.may_tune) {
                 trial = true;
             }
         }
+        // a forced window without a tuned placement sits at the mesh centre
+        if (strat == BN_STRATEGY_HYBRID && args.win_nx == 0) {
+            int wnx = 0, wny = 0;
+            if (!window_shape(grid->res[0], grid->res[1], n_attrs, sd.do_sum != 0, c->smem_optin, &wnx, &wny))
+                return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_HYBRID: at most %d attributes", kWindowMaxAttr);
+            args.win_x0 = (grid->res[0] - wnx) / 2;
+            args.win_y0 = (grid->res[1] - wny) / 2;
+            args.win_nx = wnx;
+            args.win_ny = wny;
+        }
         // min/max as global key records: the global strategy's state, and
-        // for f64 the private strategy's exact keys (behind a shared filter)
+        // for f64 the private strategy's exact keys (behind a shared filter);
+        // f64 records of three or more attributes get the 32-bit filter
+        const bool global_like = strat == BN_STRATEGY_GLOBAL || strat == BN_STRATEGY_HYBRID;
         const bool keys_private = dtype == BN_F64 && (strat == BN_STRATEGY_PRIVATE || trial);
-        if ((strat == BN_STRATEGY_GLOBAL || keys_private || trial) && !accumulate && n_attrs > 0 &&
+        if ((global_like || keys_private || trial) && !accumulate && n_attrs > 0 &&
             (want_min || want_max)) {
             sd.mmk = plan.alloc((size_t)key_record_pairs(n_attrs, (int)dtype_size(dtype)) * B * 2 *
                                 dtype_size(dtype));
             if (!sd.mmk) return cuda_fail(plan.err, "cudaMallocAsync(min/max keys)");
+            if ((global_like || trial) && dtype == BN_F64 && n_attrs >= 3) {
+                sd.mmf = plan.alloc((size_t)filter_record_pairs(n_attrs) * B * sizeof(int2));
+                if (!sd.mmf) return cuda_fail(plan.err, "cudaMallocAsync(min/max filter)");
+            }
         }
         if (strat == BN_STRATEGY_PRIVATE && private_smem_bytes(args, c->smem_optin) == 0)
             return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_PRIVATE: the mesh does not fit in shared memory");
@@ -770,9 +803,11 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
             for (const Cand& cd : cands) {
                 BinArgs ta = args;
                 ta.aggregate = aggbits == BN_AGG_ON ? 1 : aggbits == BN_AGG_OFF ? 0 : cd.agg;
-                // the key records serve the global strategy, and f64 private meshes
+                // the key records serve the global strategy, and f64 private
+                // meshes; the filter only the global strategy
                 if (cd.strat == BN_STRATEGY_SORT || (cd.strat == BN_STRATEGY_PRIVATE && dtype != BN_F64))
                     ta.st.mmk = nullptr;
+                if (cd.strat != BN_STRATEGY_GLOBAL) ta.st.mmf = nullptr;
                 auto pass = [&]() {
                     return cd.strat == BN_STRATEGY_PRIVATE ? launch_bin_private(kc, ta)
                            : cd.strat == BN_STRATEGY_SORT  ? launch_bin_sort(kc, ta, sortd, sort_scratch)
@@ -806,13 +841,10 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         // steps keep their distribution from one step to the next) and kept
         // only if it is faster.
         int wbest[4] = {0, 0, 0, 0};
-        if (e == cudaSuccess && win.strat == BN_STRATEGY_GLOBAL && private_smem_bytes(args, c->smem_optin) == 0) {
+        int wnx = 0, wny = 0;
+        if (e == cudaSuccess && win.strat == BN_STRATEGY_GLOBAL && private_smem_bytes(args, c->smem_optin) == 0 &&
+            window_shape(grid->res[0], grid->res[1], n_attrs, sd.do_sum != 0, c->smem_optin, &wnx, &wny)) {
             const int rx = grid->res[0], ry = grid->res[1];
-            int cells = 0;
-            while (global_window_bytes(cells + 64, n_attrs, sd.do_sum != 0) <= (size_t)(c->smem_optin - 2048))
-                cells += 64;
-            int side = (int)std::sqrt((double)cells);
-            const int wnx = std::min(side, rx), wny = std::min(cells / std::max(wnx, 1), ry);
             if (wnx >= 8 && wny >= 8 && (int64_t)wnx * wny < B) {
                 std::vector<unsigned long long> cnt((size_t)B);
                 e = cudaEventSynchronize(e1);
@@ -888,6 +920,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         if (e1) cudaEventDestroy(e1);
         if (e != cudaSuccess) return cuda_fail(e, "autotuner trial");
         strat = win.strat;
+        if (strat == BN_STRATEGY_GLOBAL && wbest[2] > 0) strat = BN_STRATEGY_HYBRID;
         if (!aggbits) args.aggregate = win.agg;
         {
             std::lock_guard<std::mutex> lk(c->tune_mu);
@@ -902,6 +935,8 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
             c->tune_log.push_back(std::string(head) + times + tail);
         }
         if (strat == BN_STRATEGY_SORT || (strat == BN_STRATEGY_PRIVATE && dtype != BN_F64)) sd.mmk = nullptr;
+        if (strat != BN_STRATEGY_GLOBAL && strat != BN_STRATEGY_HYBRID) sd.mmf = nullptr;
+        args.st = sd;
         e = launch_init_state(kc, dtype, sd, nullptr);
         if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     }

@@ -33,6 +33,10 @@ constexpr size_t kOffBounds = 256;   // 4 values of the coordinate type
 constexpr size_t kOffStatus = 512;   // one int
 constexpr size_t kOffEdges = 1024;   // f64 edge keys, res_x + 1 then res_y + 1
 constexpr size_t kMaxEdgeKeys = (kStaticScratchBytes - kOffEdges) / sizeof(long long);
+static_assert(sizeof(GridDesc) <= kOffBounds - kOffDesc, "mesh descriptor overruns its scratch slot");
+static_assert(4 * sizeof(double) <= kOffStatus - kOffBounds, "bounds accumulator overruns its scratch slot");
+static_assert(kOffStatus + sizeof(int) <= kOffEdges, "status word overruns its scratch slot");
+static_assert(kOffDesc % alignof(GridDesc) == 0 && kOffEdges % alignof(long long) == 0, "misaligned slot");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -177,14 +181,19 @@ extern "C" bn_status bn_bin_particles_static(const bn_buffer* x, const bn_buffer
     args.n = n;
     args.st = sd;
     args.grid = gd;
-    args.dev_grid = dev_grid;
+    // The kernels read the descriptor from the scratch array only when the
+    // device computes it (automatic bounds, f64 edge keys) or publishes the
+    // bounds; f32 data with explicit bounds passes it by value, as
+    // bn_bin_particles does.
+    const bool dev_setup = dtype == BN_F64 || grid->auto_bounds || bounds_out;
+    args.dev_grid = dev_setup ? dev_grid : nullptr;
 
     // the status word keeps the previous call's value: clear it first
     e = cudaMemsetAsync(status, 0, sizeof(int), s);
     if (e == cudaSuccess) e = launch_init_state(kc, dtype, sd, bounds_acc);
     if (e == cudaSuccess && grid->auto_bounds && n > 0)
         e = launch_bounds_reduce(kc, dtype, args.x, args.y, n, bounds_acc);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && dev_setup)
         e = launch_grid_setup(kc, dtype, gd, bounds_acc, dev_grid, dtype == BN_F64 ? e0 : nullptr,
                               dtype == BN_F64 ? e1 : nullptr, bounds_out, status);
     if (e == cudaSuccess && n > 0) {

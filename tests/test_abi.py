@@ -67,7 +67,8 @@ def test_constants_match_header(bn):
     from paper_2310_02926_gb300 import _abi
     hdr = open(_abi.HEADER).read()
     for name in ("BN_OP_COUNT", "BN_OP_AVG", "BN_OP_ACCUMULATE", "BN_SUM_F32", "BN_SUM_F64",
-                 "BN_STRATEGY_PRIVATE", "BN_STRATEGY_GLOBAL", "BN_STRATEGY_SORT"):
+                 "BN_STRATEGY_PRIVATE", "BN_STRATEGY_GLOBAL", "BN_STRATEGY_SORT",
+                 "BN_STRATEGY_HYBRID"):
         m = re.search(name + r"\s*=\s*(\d+)u?\s*<<\s*(\d+)", hdr)
         assert m, name
         assert getattr(_abi, name[3:]) == int(m.group(1)) << int(m.group(2)), name

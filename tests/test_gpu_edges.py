@@ -1,0 +1,202 @@
+"""GPU parity on and around every bin edge, for every binner.
+
+The bin index of a coordinate follows a fixed round-to-nearest sequence in
+the coordinate's own type (Sec. 4.2 bin location; the sequence is the
+oracle's reading R1). Each binner has its own code for it: the f32 floor
+trick (`round_small` in the f32 axis), the f64 edge keys, and the copies of
+both inside the persistent batch kernel, the sort pass and the fused
+multi-grid pass. These tests put particles on every edge and within three
+units in the last place on either side of it, in f32 and in f64, and run
+them through bn_bin_particles (private, global, sort and hybrid strategies),
+bn_bin_batch, bn_bin_multi and bn_bin_particles_static; counts, min and max
+must equal the oracle bit for bit and sums must stay within tolerance.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from _parity import TOL_F32C, TOL_F64, abs_sums, assert_parity, run_gpu, to_numpy_result
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# (lo, hi, res) per axis pair. Each stresses a different part of the index:
+# a large mesh, non-dyadic widths, meshes of a few bins, a bin a few ulp wide
+# (f32 near 1e3: ulp 6.1e-5 against 1e-3-wide bins), an offset axis whose
+# width is exact in f64 but not in f32, and the 4096^2 mesh of the Gaussian
+# workload.
+F32_GRIDS = [
+    ((-10.0, -10.0), (10.0, 10.0), (1024, 1024)),
+    ((-1.3, 0.1), (2.7, 0.35), (37, 5)),
+    ((0.0, 0.0), (1.0, 1.0), (3, 7)),
+    ((1e3, -3.0), (1e3 + 1.0, 3.0), (1000, 3)),
+    ((-1e-3, 5.0), (2e-3, 5.001), (999, 17)),
+    ((0.0, 0.0), (1.0, 1.0), (4096, 4096)),
+]
+F64_GRIDS = [
+    ((-10.0, -10.0), (10.0, 10.0), (1024, 1024)),
+    ((-1.3, 0.1), (2.7, 0.35), (37, 5)),
+    ((1e6, -3.0), (1e6 + 1.0, 3.0), (1000, 3)),
+    ((-1e-3, 5.0), (2e-3, 5.0 + 1e-9), (999, 17)),
+]
+
+
+@pytest.fixture(scope="module")
+def bn():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2310_02926_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(bn):
+    c = bn.Context(0)
+    yield c
+    c.close()
+
+
+def edge_workload(grid, dtype, seed, repeat=3):
+    """Particles on every edge (every edge for meshes up to 1024 bins per
+    axis, every 8th above) and within 3 ulp of it in `dtype`, the other
+    coordinate uniform; the set is repeated with fresh partners so the
+    vector loads and the scalar tails both see edge values."""
+    lo, hi, res = grid
+    T = np.dtype(dtype).type
+    pts = []
+    for a in range(2):
+        lo_t, hi_t = T(lo[a]), T(hi[a])
+        s_t = T(T(res[a]) / T(hi_t - lo_t))
+        step = 1 if res[a] <= 1024 else 8
+        for i in range(0, res[a] + 1, step):
+            # the edge estimate lo + i / s in T, then +-3 ulp around it
+            e = T(lo_t + T(T(i) / s_t))
+            for k in range(-3, 4):
+                v = e
+                for _ in range(abs(k)):
+                    v = np.nextafter(v, T(np.inf) if k > 0 else T(-np.inf))
+                pts.append((a, v))
+    rng = np.random.default_rng(seed)
+    n = len(pts) * repeat
+    x = rng.uniform(lo[0], hi[0], n).astype(dtype)
+    y = rng.uniform(lo[1], hi[1], n).astype(dtype)
+    for r in range(repeat):
+        for k, (a, v) in enumerate(pts):
+            (x if a == 0 else y)[r * len(pts) + k] = v
+    perm = rng.permutation(n)
+    x, y = x[perm], y[perm]
+    m = rng.uniform(1.0, 2.0, n).astype(dtype)
+    q = rng.standard_normal(n).astype(dtype)
+    return workloads.Workload("edges", x, y, [m, q], lo, hi, res)
+
+
+def check(w, gpu, tol, label):
+    ref = oracle.bin_workload(w, False)
+    assert_parity(gpu, ref, abs_sums(w), tol, label=label)
+
+
+def tol_of(dtype):
+    return TOL_F64 if dtype == np.float64 else TOL_F32C
+
+
+def mesh_fits_private(res, dtype):
+    # count, compensated sums and min/max keys of two attributes per bin
+    return res[0] * res[1] * (4 + 2 * 8 + 2 * 2 * np.dtype(dtype).itemsize) <= 200_000
+
+
+CASES = [(np.float32, g) for g in F32_GRIDS] + [(np.float64, g) for g in F64_GRIDS]
+IDS = [f"{np.dtype(d).name}-{g[2][0]}x{g[2][1]}-{g[0][0]:g}" for d, g in CASES]
+
+
+@pytest.mark.parametrize("dtype,grid", CASES, ids=IDS)
+@pytest.mark.parametrize("strategy", ["private", "global", "sort", "hybrid"])
+def test_edges_bin_particles(bn, ctx, dtype, grid, strategy):
+    if strategy == "private" and not mesh_fits_private(grid[2], dtype):
+        pytest.skip("mesh does not fit shared memory")
+    w = edge_workload(grid, dtype, seed=101)
+    flags = {"private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL,
+             "sort": bn.STRATEGY_SORT, "hybrid": bn.STRATEGY_HYBRID}[strategy]
+    check(w, run_gpu(ctx, w, flags=flags), tol_of(dtype), f"{strategy}")
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("strategy", ["auto", "private", "global", "sort"])
+def test_edges_bin_batch(bn, ctx, dtype, strategy):
+    """Every edge grid of the dtype as one block of a single persistent
+    batch launch."""
+    grids = F32_GRIDS if dtype == np.float32 else F64_GRIDS
+    if strategy == "private":
+        grids = [g for g in grids if mesh_fits_private(g[2], dtype)]
+    flags = {"auto": 0, "private": bn.STRATEGY_PRIVATE, "global": bn.STRATEGY_GLOBAL,
+             "sort": bn.STRATEGY_SORT}[strategy]
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    blocks, outs, keep = [], [], []
+    for k, g in enumerate(grids):
+        w = edge_workload(g, dtype, seed=200 + k)
+        cols = [torch.from_numpy(c).cuda() for c in (w.x, w.y, *w.attrs)]
+        o = bn.alloc_outputs(2, w.res[0] * w.res[1], tdt, torch.device("cuda"))
+        r = bn.result_struct(o)
+        keep += [cols, r]
+        outs.append((w, o))
+        blocks.append(bn.block(cols[0], cols[1], cols[2:], bn.grid(w.lo, w.hi, w.res), r))
+    bn.bn_bin_batch(ctx.handle, blocks, bn.OP_ALL | flags)
+    torch.cuda.synchronize()
+    for k, (w, o) in enumerate(outs):
+        check(w, to_numpy_result(o), tol_of(dtype), f"batch {strategy} block {k}")
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_edges_bin_multi(bn, ctx, dtype):
+    """Every edge grid of the dtype as one spec of a fused multi-grid pass:
+    the columns hold each grid's edge set in turn (x0, y0, x1, y1, ...)
+    plus the two attributes of the first."""
+    grids = F32_GRIDS if dtype == np.float32 else F64_GRIDS
+    ws = [edge_workload(g, dtype, seed=300 + k) for k, g in enumerate(grids)]
+    n = min(w.n for w in ws)
+    cols = []
+    for w in ws:
+        cols += [w.x[:n], w.y[:n]]
+    attrs = [ws[0].attrs[0][:n], ws[0].attrs[1][:n]]
+    cols += attrs
+    ia = [len(cols) - 2, len(cols) - 1]
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    tcols = [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in cols]
+    specs, outs, keep = [], [], []
+    for k, (lo, hi, res) in enumerate(grids):
+        specs.append(bn.grid_spec(2 * k, 2 * k + 1, ia, bn.grid(lo, hi, res)))
+        o = bn.alloc_outputs(2, res[0] * res[1], tdt, torch.device("cuda"))
+        keep.append(o)
+        outs.append(bn.result_struct(o))
+    bn.bn_bin_multi(ctx.handle, tcols, specs, bn.OP_ALL, outs)
+    torch.cuda.synchronize()
+    for k, (lo, hi, res) in enumerate(grids):
+        w = workloads.Workload(f"spec{k}", cols[2 * k], cols[2 * k + 1], attrs, lo, hi, res)
+        # the fused pass accumulates in FP64 for both dtypes
+        check(w, to_numpy_result(keep[k]), TOL_F64, f"multi spec {k}")
+
+
+@pytest.mark.parametrize("dtype,grid", CASES, ids=IDS)
+def test_edges_static_entry(bn, dtype, grid):
+    """The no-allocation entry point on the same edge sets."""
+    if dtype == np.float64 and grid[2][0] + grid[2][1] > 8062:
+        pytest.skip("f64 mesh above the no-allocation entry point's edge-key limit")
+    w = edge_workload(grid, dtype, seed=401)
+    dev = torch.device("cuda", 0)
+    cols = [torch.from_numpy(c).to(dev) for c in (w.x, w.y, *w.attrs)]
+    B = w.res[0] * w.res[1]
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    out = bn.alloc_outputs(2, B, tdt, dev)
+    arr = (bn.bn_buffer * 2)(*[bn.buffer(c) for c in cols[2:]])
+    r = bn.result_struct(out)
+    g = bn.grid(w.lo, w.hi, w.res)
+    st = bn.lib().bn_bin_particles_static(ctypes.byref(bn.buffer(cols[0])),
+                                          ctypes.byref(bn.buffer(cols[1])), arr, 2,
+                                          ctypes.byref(g), bn.OP_ALL, ctypes.byref(r),
+                                          torch.cuda.current_stream().cuda_stream, 1)
+    assert st == bn.OK, bn.lib().bn_last_error()
+    check(w, to_numpy_result(out), tol_of(dtype), "static")

@@ -51,7 +51,8 @@ def test_uniform64_f64_config(bn, ctx, strategy):
     check(w, run_gpu(ctx, w, flags=flags), TOL_F64, label=strategy)
 
 
-STRAT = {"auto": 0, "private": "STRATEGY_PRIVATE", "global": "STRATEGY_GLOBAL", "sort": "STRATEGY_SORT"}
+STRAT = {"auto": 0, "private": "STRATEGY_PRIVATE", "global": "STRATEGY_GLOBAL", "sort": "STRATEGY_SORT",
+         "hybrid": "STRATEGY_HYBRID"}
 
 
 def sflag(bn, name):
@@ -59,7 +60,7 @@ def sflag(bn, name):
     return v if isinstance(v, int) else getattr(bn, v)
 
 
-@pytest.mark.parametrize("strategy", ["auto", "global", "sort"])
+@pytest.mark.parametrize("strategy", ["auto", "global", "sort", "hybrid"])
 def test_plummer_f64_reduced(bn, ctx, strategy):
     """Plummer sphere projected on x-y, 3 f64 attributes, 1024x1024 over [-10,10]^2."""
     w = workloads.plummer(2_000_003, seed=1, dtype=np.float64, res=1024)
@@ -113,7 +114,69 @@ def test_global_key_records_any_attribute_count(bn, ctx, dtype, n_attrs, aggrega
     check(w, run_gpu(ctx, w, flags=flags), TOL_F64 if dtype == np.float64 else TOL_F32C)
 
 
-@pytest.mark.parametrize("strategy", ["private", "global"])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("n_attrs", [0, 1, 2, 3, 4])
+def test_hybrid_window_any_attribute_count(bn, ctx, dtype, n_attrs):
+    """Hybrid strategy: a centred shared-memory window (fixed-point sums)
+    plus global atomics around it; particles both inside and outside it,
+    every attribute count the window kernel is compiled for."""
+    w = workloads.plummer(400_001, seed=80 + n_attrs, dtype=dtype, res=1024)
+    rng = np.random.default_rng(90 + n_attrs)
+    w.attrs = [rng.standard_normal(w.n).astype(dtype) * 10.0 ** k for k in range(n_attrs)]
+    if n_attrs == 0:
+        got = run_gpu(ctx, w, ops=bn.OP_COUNT, flags=bn.STRATEGY_HYBRID)
+        np.testing.assert_array_equal(got["count"], oracle.bin_workload(w)["count"])
+        return
+    check(w, run_gpu(ctx, w, flags=bn.STRATEGY_HYBRID), TOL_F64 if dtype == np.float64 else TOL_F32C)
+
+
+def test_hybrid_rejects_more_than_four_attributes(bn, ctx):
+    w = workloads.plummer(10_000, seed=3, dtype=np.float64, res=64)
+    w.attrs = [w.x.copy() for _ in range(5)]
+    with pytest.raises(bn.BinningError) as e:
+        run_gpu(ctx, w, flags=bn.STRATEGY_HYBRID)
+    assert e.value.code == bn.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_hybrid_fixed_point_ranges(bn, ctx, dtype):
+    """Window sums are fixed-point integers with a scale chosen from the
+    first values each CTA reads. Values outside that scale's range (tiny,
+    huge, subnormal, +-inf, NaN), signed zeros, long runs of carries and
+    borrows, and a second half of the input a million times larger than the
+    sampled first half all go through it; counts, min and max stay exact,
+    sums within tolerance, integer-valued sums exact."""
+    rng = np.random.default_rng(123)
+    n = 600_001
+    half = n // 2
+    x = np.clip(rng.normal(0.5, 0.02, n), 0.0, 0.999).astype(dtype)
+    y = np.clip(rng.normal(0.5, 0.02, n), 0.0, 0.999).astype(dtype)
+    big = np.float64(2.0 ** 100 if dtype == np.float64 else 2.0 ** 60)
+    wide = (rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-30, 30, n)).astype(dtype)
+    carry = np.where(np.arange(n) % 2 == 0, 1.0, -1.0) * (1.75 + rng.random(n) * 1e-3)
+    carry = carry.astype(dtype)
+    special = rng.uniform(-1, 1, n).astype(dtype)
+    special[::101] = np.nan
+    special[1::103] = np.inf
+    special[2::107] = -np.inf
+    special[3::109] = -0.0
+    special[4::113] = 0.0
+    special[5::127] = np.finfo(dtype).smallest_subnormal
+    special[6::131] = -np.finfo(dtype).smallest_subnormal
+    special[7::137] = big
+    step = np.where(np.arange(n) < half, 1e-3, 1e3).astype(dtype) * rng.uniform(1, 2, n).astype(dtype)
+    ones = np.ones(n, dtype=dtype)
+    w = workloads.Workload("ranges", x, y, [wide, carry, special, step], (0.0, 0.0), (1.0, 1.0),
+                           (512, 512))
+    gpu = run_gpu(ctx, w, flags=bn.STRATEGY_HYBRID)
+    check(w, gpu, TOL_F64 if dtype == np.float64 else TOL_F32C)
+    w1 = workloads.Workload("ones", x, y, [ones], (0.0, 0.0), (1.0, 1.0), (512, 512))
+    g1 = run_gpu(ctx, w1, flags=bn.STRATEGY_HYBRID)
+    ref = oracle.bin_workload(w1)
+    np.testing.assert_array_equal(g1["sum"][0], ref["sum"][0])
+
+
+@pytest.mark.parametrize("strategy", ["private", "global", "hybrid"])
 def test_min_max_with_tied_extremes(bn, ctx, strategy):
     """Attributes whose values tie at a bin's extreme (a constant column, a
     two-valued column, signed zeros): every tied particle reaches the exact
@@ -175,7 +238,7 @@ def test_gaussians_f32_sum_modes(bn, ctx, res, strategy, mode):
 
 # ------------------------------------------------------------------ edge cases
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("strategy", ["private", "global", "sort"])
+@pytest.mark.parametrize("strategy", ["private", "global", "sort", "hybrid"])
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 31, 33, 1023, 1025, 4095, 4097, 70_001])
 def test_ragged_lengths(bn, ctx, dtype, strategy, n):
     w = workloads.uniform(n, seed=4 + n, dtype=dtype, res=16)
@@ -185,7 +248,7 @@ def test_ragged_lengths(bn, ctx, dtype, strategy, n):
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("strategy", ["private", "global", "sort"])
+@pytest.mark.parametrize("strategy", ["private", "global", "sort", "hybrid"])
 @pytest.mark.parametrize("offsets", [(1, 1, 1, 1), (1, 2, 3, 0), (3, 3, 3, 3)])
 def test_misaligned_columns(bn, ctx, dtype, strategy, offsets):
     """Sub-range views whose starts are not 16-byte aligned (same or mixed phase)."""
@@ -214,7 +277,7 @@ def test_strided_columns(bn, ctx, dtype):
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("strategy", ["private", "global", "sort"])
+@pytest.mark.parametrize("strategy", ["private", "global", "sort", "hybrid"])
 def test_special_values(bn, ctx, dtype, strategy):
     rng = np.random.default_rng(7)
     n = 20_000
@@ -251,7 +314,7 @@ F64_GRIDS = [
 
 
 @pytest.mark.parametrize("grid", F64_GRIDS)
-@pytest.mark.parametrize("strategy", ["private", "global", "sort"])
+@pytest.mark.parametrize("strategy", ["private", "global", "sort", "hybrid"])
 def test_f64_bin_edges_exact(bn, ctx, grid, strategy):
     """Particles on and within a few ulp of every bin edge: indices must
     follow the round-to-nearest sequence exactly (via the edge-key method)."""
@@ -282,7 +345,7 @@ def test_f64_bin_edges_exact(bn, ctx, grid, strategy):
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("strategy", ["private", "global", "sort"])
+@pytest.mark.parametrize("strategy", ["private", "global", "sort", "hybrid"])
 def test_auto_bounds(bn, ctx, dtype, strategy):
     w = workloads.plummer(300_001, seed=9, dtype=dtype, res=40)
     w.x[::1000] = np.nan
@@ -324,7 +387,7 @@ def test_host_inputs_and_outputs(bn, ctx):
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("strategy", ["auto", "private", "global", "sort"])
+@pytest.mark.parametrize("strategy", ["auto", "private", "global", "sort", "hybrid"])
 @pytest.mark.parametrize("auto_bounds", [False, True])
 def test_pinned_host_columns_read_in_place(bn, ctx, dtype, strategy, auto_bounds):
     """Page-locked host columns are read by the kernels over the host link;
@@ -376,7 +439,7 @@ def test_library_allocated_outputs(bn, ctx):
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("strategy", ["auto", "private", "global", "sort"])
+@pytest.mark.parametrize("strategy", ["auto", "private", "global", "sort", "hybrid"])
 def test_accumulate_shards_into_one_state(bn, ctx, dtype, strategy):
     """Shards binned one after another into the same outputs (BN_OP_ACCUMULATE)
     equal the whole set binned at once, whatever strategy each shard takes."""
