@@ -36,9 +36,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("binned particles/s and % of HBM peak, batched FP32 vs plain FP64; p99 latency")
 UNIT = "particles/s"
-N_PART = 50_000_000
-RES = 1024
-N_ATTR = 3
 
 # name -> (generator, default particles, mesh side, attributes, dtype label, description)
 WORKLOADS = {
@@ -231,9 +228,14 @@ def run_reference(args):
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": WORKLOADS[args.workload][4],
             "data": "synthetic", "impl": "reference",
-            "config": workload_config(args.workload, WORKLOADS[args.workload][1], w.bytes_read()),
+            "config": {k: v for k, v in workload_config(args.workload, WORKLOADS[args.workload][1],
+                                                         w.bytes_read()).items() if k != "l2"} | {
+                "sample_particles_per_step": sample_n,
+                "timed": f"the CPU oracle (single thread) on a {sample_n:,}-particle draw of the same "
+                         f"workload (same generator and seed) per step; particles/s is sample "
+                         f"particles / time"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{sample_n:,} particles of the same workload per step"},
+                             "sample": f"a {sample_n:,}-particle draw of the same workload per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -303,18 +305,22 @@ def run_batch(args, n_blocks):
                                          "private": bn.STRATEGY_PRIVATE,
                                          "sort": bn.STRATEGY_SORT, "hybrid": bn.STRATEGY_HYBRID}[args.strategy]
 
-        def timed(fn, steps, warm):
-            reqs = []
+        clocks = ClockSampler(0).start()
+        walls = {}
+
+        def timed(fn, steps, warm, key):
             for _ in range(warm):
                 fn()
             stream.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             l0 = ctx.launches
+            t_a = time.time()
             e0.record(stream)
             for _ in range(steps):
                 fn()
             e1.record(stream)
             e1.synchronize()
+            walls[key] = (t_a, time.time())
             return e0.elapsed_time(e1) / steps, (ctx.launches - l0) // steps
 
         # request handles of asynchronous calls are freed as they complete
@@ -327,8 +333,11 @@ def run_batch(args, n_blocks):
                 q = bn.bn_bin_particles(ctx.handle, c64[0], c64[1], c64[2:], g, bn.OP_ALL, r, sync=False)
                 bn.bn_request_release(q)
 
-        ms_b, launches_b = timed(batched, args.steps, args.warmup)
-        ms_p, launches_p = timed(plain, max(1, args.steps // 4), 1)
+        ms_b, launches_b = timed(batched, args.steps, args.warmup, "batched")
+        ms_p, launches_p = timed(plain, max(3, args.steps // 4), 3, "plain")
+        time.sleep(0.3)
+        clocks.stop()
+        clk = clocks.summary(walls["batched"][0], walls["plain"][1])
     bytes32 = total * 16
     bins_total = sum(int(plan.sides[k]) ** 2 for k in range(plan.n_blocks))
     out_bytes = bins_total * (8 + 2 * (8 + 4 + 4 + 8))   # count, and sum/min/max/avg per attribute
@@ -350,20 +359,32 @@ def run_batch(args, n_blocks):
             "speedup_batched_fp32_vs_plain_fp64": ms_p / ms_b,
             "bins_total": bins_total, "output_bytes": out_bytes,
             "autotuner": tuning,
-            "data_generation_s": gen_s}
+            "data_generation_s": gen_s,
+            "gpu_launches": launches_b * args.steps,
+            "clocks": clk}
     if args.check:
-        worst = 0.0
-        exact = True
-        for k in range(plan.n_blocks):
-            w = plan.block(k)
-            o = {kk: vv for kk, vv in keep[k][1].items()}
+        # blocks in a seeded random order, each against the oracle, until the
+        # time budget is spent (the sample is stated in the result)
+        import numpy as np
+        order = np.random.default_rng(7).permutation(plan.n_blocks)
+        worst, exact, checked, parts = 0.0, True, 0, 0
+        t_chk = time.time()
+        for k in order:
+            if checked and time.time() - t_chk > args.check_seconds:
+                break
+            w = plan.block(int(k))
+            o = {kk: vv for kk, vv in keep[int(k)][1].items()}
             e = compare_with_oracle(w, o, bn)
             worst = max(worst, e["sum_rel_err_max"])
             exact = exact and e["count_exact"] and all(v for kk, v in e.items() if kk.endswith("_exact"))
-        line["errors_vs_oracle"] = {"exact_count_min_max": exact, "sum_rel_err_max": worst}
-    print(json.dumps(line), flush=True)
+            checked += 1
+            parts += w.n
+        line["errors_vs_oracle"] = {
+            "exact_count_min_max": exact, "sum_rel_err_max": worst, "tolerance": 1e-6,
+            "sample": f"{checked} of {plan.n_blocks} blocks ({parts:,} of {total:,} particles), "
+                      f"seeded random order, {args.check_seconds:.0f} s budget"}
     ctx.close()
-    return 0
+    return line
 
 
 def run_multigrid(args, n):
@@ -461,9 +482,8 @@ def run_multigrid(args, n):
             worst = max(worst, e["sum_rel_err_max"])
             exact = exact and all(v for kk, v in e.items() if kk.endswith("_exact"))
         line["errors_vs_oracle"] = {"exact_count_min_max": exact, "sum_rel_err_max": worst}
-    print(json.dumps(line), flush=True)
     ctx.close()
-    return 0
+    return line
 
 
 def run_serving(args, n_requests):
@@ -535,7 +555,9 @@ def run_serving(args, n_requests):
         th.start()
         time.sleep(0.5)
     prod_times.clear()
-    lat, outstanding, served = [], [], 0
+    lat, outstanding, served, parts = [], [], 0, []
+    clocks = ClockSampler(0).start()
+    t_wall0 = time.time()
     t_start = time.perf_counter()
     i = 0
     while i < plan.n_requests or outstanding:
@@ -548,8 +570,9 @@ def run_serving(args, n_requests):
             r = bn.result_struct(o, stream=0)
             blk = bn.block(*[c[o0:o0 + n] for c in pool[:2]], [c[o0:o0 + n] for c in pool[2:]],
                            bn.grid((-10, -10), (10, 10), (side, side)), r, stream=0)
+            t_call = time.perf_counter() - t_start
             req = bn.bn_server_submit(srv, blk, bn.OP_ALL)
-            outstanding.append((req, plan.arrival_s[i], n, sl, r, blk))
+            outstanding.append((req, plan.arrival_s[i], n, sl, r, blk, t_call - plan.arrival_s[i]))
             i += 1
         keep = []
         now = time.perf_counter() - t_start
@@ -561,11 +584,18 @@ def run_serving(args, n_requests):
             if st < 0:
                 raise RuntimeError(f"request failed: {st}")
             lat.append(now - item[1])
+            tm = bn.bn_server_request_timing(item[0]) or {}
+            tm["lag_us"] = 1e6 * item[6]
+            parts.append(tm)
             served += item[2]
             free.append(item[3])
             bn.bn_request_release(item[0])
         outstanding = keep
     wall = time.perf_counter() - t_start
+    t_wall1 = time.time()
+    time.sleep(0.3)
+    clocks.stop()
+    clk = clocks.summary(t_wall0, t_wall1)
     stop.set()
     if not args.no_producer:
         th.join()
@@ -574,6 +604,18 @@ def run_serving(args, n_requests):
     bn.bn_server_destroy(srv)
     ctx.close()
     lat_ms = np.array(lat) * 1e3
+    # where the time goes: the bench's own lag before submit (an output slot
+    # to reuse, the polling loop), then the server's record of each stage
+    comp = {"bench_lag": "lag_us", "submit": "submit_us", "queue": "queue_us", "launch": "launch_us",
+            "complete": "complete_us", "batch_gpu": "batch_gpu_us"}
+    cols = {k: np.array([p.get(v, 0.0) for p in parts]) / 1e3 for k, v in comp.items()}
+    accounted = sum(cols[k] for k in ("bench_lag", "submit", "queue", "launch", "complete"))
+    cols["poll"] = np.maximum(lat_ms - accounted, 0.0)
+    tail = lat_ms >= np.percentile(lat_ms, 99)
+    split = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)),
+                 "mean_in_p99_tail": float(v[tail].mean())} for k, v in cols.items()}
+    split["batch_size"] = {"p50": float(np.percentile([p.get("batch_size", 0) for p in parts], 50)),
+                           "max": float(max(p.get("batch_size", 0) for p in parts))}
     line = {"metric": METRIC, "value": served / wall, "unit": UNIT, "n_gpus": 1,
             "steps": plan.n_requests, "warmup": 0, "ms_per_step": wall * 1e3 / plan.n_requests,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -586,74 +628,43 @@ def run_serving(args, n_requests):
             "particles_served": int(served), "wall_s": wall,
             "producer_step_ms": {"alone": float(np.median(alone)) if alone else None,
                                  "with_serving": float(np.median(with_serving)) if with_serving else None},
-            "server": stats}
-    print(json.dumps(line), flush=True)
-    return 0
+            "latency_split_ms": split,
+            "server": stats,
+            "clocks": clk}
+    return line
 
 
-def main():
-    global N_PART
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--reference-sample", type=int, default=2_000_000)
-    ap.add_argument("--strategy", default="auto", choices=["auto", "global", "private", "sort", "hybrid"])
-    ap.add_argument("--workload", default="plummer1024", choices=sorted(WORKLOADS))
-    ap.add_argument("--n", type=int, default=0,
-                    help="particles (0 = the workload's size; smaller cases for profiling runs)")
-    ap.add_argument("--sum", default="f32c", choices=["f32c", "f32", "f64"],
-                    help="sum mode for f32 workloads")
-    ap.add_argument("--serving-priority", default="high", choices=["low", "high"],
-                    help="stream priority of the server relative to the producer")
-    ap.add_argument("--no-producer", action="store_true", help="serving without the producer")
-    ap.add_argument("--ops", default="all", choices=["all", "count", "count+sum", "count+minmax"],
-                    help="reductions to compute (all = count/sum/min/max/avg, the benchmark's)")
-    ap.add_argument("--multigrid-vars", type=int, default=10, choices=range(1, 11),
-                    help="multigrid workload: variables binned in every coordinate system")
-    ap.add_argument("--multigrid-res", type=int, default=256,
-                    help="multigrid workload: mesh side of every coordinate system")
-    ap.add_argument("--check", action="store_true",
-                    help="compare the last step with the CPU oracle and report per-bin errors")
-    args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
-    if args.impl == "reference":
-        return run_reference(args)
-    N_PART = args.n or WORKLOADS[args.workload][1]
-    if args.workload == "batch256":
-        return run_batch(args, N_PART)
-    if args.workload == "serving":
-        return run_serving(args, N_PART)
-    if args.workload == "multigrid":
-        return run_multigrid(args, N_PART)
+def time_threaded_baseline(w, min_seconds: float, max_reps: int):
+    """The all-core CPU baseline (oracle/binning_threaded.c) on the whole
+    workload: particles/s and the threads it used."""
+    import oracle
+    threads = len(os.sched_getaffinity(0))
+    oracle.bin_particles_threaded(w.x[:1000], w.y[:1000], [a[:1000] for a in w.attrs], w.lo, w.hi,
+                                  w.res, threads=threads)  # load + warm
+    reps, t = 0, 0.0
+    while reps < max_reps and (t < min_seconds or reps == 0):
+        t0 = time.perf_counter()
+        oracle.bin_particles_threaded(w.x, w.y, w.attrs, w.lo, w.hi, w.res, threads=threads)
+        t += time.perf_counter() - t0
+        reps += 1
+    return w.n * reps / t, reps, t, threads
 
+
+def run_single(args, name, n, env, with_e2e=True, with_cpu=True, check=False, steps=None):
+    """One bn_bin_particles call per step on a single workload; returns the
+    JSON object (the headline line, or a sub-object of it)."""
     import numpy as np
     import torch
-
-    import __graft_entry__
-    __graft_entry__.build()
     import paper_2310_02926_gb300 as bn
-    import workloads
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
+    rank, world, local, pg = env
+    steps = steps or args.steps
     dev = torch.device("cuda", local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-        pg = dist
-
-    w = make_workload(args.workload, N_PART, seed=rank)
-    RES = w.res[0]
-    N_ATTR = len(w.attrs)
-    B = RES * RES
+    w = make_workload(name, n, seed=rank)
+    B = w.res[0] * w.res[1]
+    n_attr = len(w.attrs)
     tdtype = torch.float64 if w.x.dtype == np.float64 else torch.float32
-    dt_label = WORKLOADS[args.workload][4]
+    dt_label = WORKLOADS[name][4]
     stream = torch.cuda.Stream(device=dev)
     cols = [torch.from_numpy(c).to(dev) for c in (w.x, w.y, *w.attrs)]
     ctx = bn.Context(local, stream=stream.cuda_stream, profile=True)
@@ -662,12 +673,10 @@ def main():
     op_bits = {"all": bn.OP_ALL, "count": bn.OP_COUNT, "count+sum": bn.OP_COUNT | bn.OP_SUM,
                "count+minmax": bn.OP_COUNT | bn.OP_MIN | bn.OP_MAX}[args.ops]
     ops = op_bits | flags | {"f32c": bn.SUM_F32C, "f32": bn.SUM_F32, "f64": bn.SUM_F64}[args.sum]
-    if args.ops != "all":
-        args.check = False
     g = bn.grid(w.lo, w.hi, w.res)
     torch.cuda.synchronize(dev)
     with torch.cuda.stream(stream):
-        out = bn.alloc_outputs(N_ATTR, B, tdtype, dev, ops=op_bits)
+        out = bn.alloc_outputs(n_attr, B, tdtype, dev, ops=op_bits)
         res_struct = bn.result_struct(out)
 
         def step():
@@ -686,7 +695,7 @@ def main():
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t_wall0 = time.time()
         ev0.record(stream)
-        reqs = [step() for _ in range(args.steps)]
+        reqs = [step() for _ in range(steps)]
         ev1.record(stream)
         ev1.synchronize()
         t_wall1 = time.time()
@@ -707,23 +716,23 @@ def main():
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         elapsed_ms = float(t.item())
 
-    value = N_PART * args.steps * world / (elapsed_ms / 1e3)
+    value = n * steps * world / (elapsed_ms / 1e3)
     bytes_in = w.bytes_read()
     tsz = w.x.dtype.itemsize
-    bytes_state = B * (8 + N_ATTR * (8 + 2 * tsz))   # count, sum, min, max
+    bytes_state = B * (8 + n_attr * (8 + 2 * tsz))   # count, sum, min, max
     bytes_out = w.bytes_written()                    # + avg
     hbm, peak_src = peaks()
-    step_gbs = (bytes_in + bytes_out) / (elapsed_ms / args.steps / 1e3) / 1e9
+    step_gbs = (bytes_in + bytes_out) / (elapsed_ms / steps / 1e3) / 1e9
     kern_avg_ms = kern_ms / max(1, kern_launches)
     kern_bytes = bytes_in + bytes_state
     achieved = kern_bytes / (kern_avg_ms / 1e3) / 1e9 if kern_launches else None
-    traffic, traffic_note = ncu_traffic(args.workload, strategy, N_PART)
+    traffic, traffic_note = ncu_traffic(name, strategy, n)
 
     # end to end through the public API with pinned host buffers
     e2e = None
-    if args.e2e_steps > 0 and rank == 0:
+    if with_e2e and args.e2e_steps > 0 and rank == 0:
         hcols = [torch.from_numpy(c).pin_memory() for c in (w.x, w.y, *w.attrs)]
-        hout = bn.alloc_outputs(N_ATTR, B, tdtype, torch.device("cpu"), ops=op_bits)
+        hout = bn.alloc_outputs(n_attr, B, tdtype, torch.device("cpu"), ops=op_bits)
         for k in list(hout):
             hout[k] = [t.pin_memory() for t in hout[k]] if isinstance(hout[k], list) else hout[k].pin_memory()
         ctx.bin_particles(hcols[0], hcols[1], hcols[2:], w.lo, w.hi, w.res, ops=ops, out=hout)
@@ -732,45 +741,133 @@ def main():
             ctx.bin_particles(hcols[0], hcols[1], hcols[2:], w.lo, w.hi, w.res, ops=ops, out=hout)
         t_e2e = (time.perf_counter() - t0) / args.e2e_steps
         bn.bn_context_profile(ctx.handle)
-        e2e = {"value": N_PART / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_in,
+        e2e = {"value": n / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_in,
                "d2h_bytes_per_step": bytes_out, "ms_per_step": 1e3 * t_e2e}
 
     errors = None
-    if args.check and rank == 0:
+    if check and rank == 0:
         errors = compare_with_oracle(w, out, bn)
+        errors["tolerance"] = 1e-12 if dt_label == "f64" else 1e-6
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, reps, secs = time_oracle(w, min_seconds=10.0, max_reps=4)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"the full workload ({N_PART:,} particles) x {reps}, {secs:.1f} s"}
+    cpu = cpu1 = None
+    if with_cpu and rank == 0 and world == 1:
+        v, reps, secs, threads = time_threaded_baseline(w, min_seconds=5.0, max_reps=20)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "variant": "all-core FP64 oracle: per-thread private meshes, then a merge "
+                          "(oracle/binning_threaded.c)",
+               "sample": f"the full workload ({n:,} particles) x {reps}, {secs:.1f} s"}
+        v1, reps1, secs1 = time_oracle(w, min_seconds=5.0, max_reps=4)
+        cpu1 = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"the full workload ({n:,} particles) x {reps1}, {secs1:.1f} s"}
 
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": dt_label, "data": "synthetic",
-            "config": dict(workload_config(args.workload, N_PART, bytes_in), strategy=strategy,
-                           autotuner=tuning, ops=args.ops,
-                           sum_mode=args.sum if dt_label == "f32" else "f64",
-                           parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
-            "hbm_frac_step": step_gbs / hbm,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-                         "kernel": f"particle pass ({strategy} strategy)",
-                         "algorithmic_bytes_per_launch": kern_bytes,
-                         "avg_launch_ms": kern_avg_ms, "peak_source": peak_src,
-                         "traffic_note": traffic_note},
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": gpu_launches,
-            "clocks": clk,
-        }
-        if errors is not None:
-            line["errors_vs_oracle"] = errors
-        print(json.dumps(line), flush=True)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dt_label, "data": "synthetic",
+        "config": dict(workload_config(name, n, bytes_in), strategy=strategy,
+                       autotuner=tuning, ops=args.ops,
+                       sum_mode=args.sum if dt_label == "f32" else "f64",
+                       parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "hbm_frac_step": step_gbs / hbm,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                     "kernel": f"particle pass ({strategy} strategy)",
+                     "algorithmic_bytes_per_launch": kern_bytes,
+                     "avg_launch_ms": kern_avg_ms, "peak_source": peak_src,
+                     "traffic_note": traffic_note},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+    }
+    if cpu1 is not None:
+        line["cpu_baseline_1core"] = cpu1
+    if errors is not None:
+        line["errors_vs_oracle"] = errors
     ctx.close()
+    del cols, out
+    torch.cuda.empty_cache()
+    return line
+
+
+def sub_object(line, keep=("value", "unit", "ms_per_step", "steps", "dtype", "config", "roofline",
+                           "clocks", "errors_vs_oracle", "gpu_launches")):
+    return {k: line[k] for k in keep if k in line}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only: skip the uniform-at-scale, batch and serving sub-objects")
+    ap.add_argument("--reference-sample", type=int, default=2_000_000)
+    ap.add_argument("--strategy", default="auto", choices=["auto", "global", "private", "sort", "hybrid"])
+    ap.add_argument("--workload", default="plummer1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=0,
+                    help="particles (0 = the workload's size; smaller cases for profiling runs)")
+    ap.add_argument("--sum", default="f32c", choices=["f32c", "f32", "f64"],
+                    help="sum mode for f32 workloads")
+    ap.add_argument("--serving-priority", default="high", choices=["low", "high"],
+                    help="stream priority of the server relative to the producer")
+    ap.add_argument("--no-producer", action="store_true", help="serving without the producer")
+    ap.add_argument("--ops", default="all", choices=["all", "count", "count+sum", "count+minmax"],
+                    help="reductions to compute (all = count/sum/min/max/avg, the benchmark's)")
+    ap.add_argument("--multigrid-vars", type=int, default=10, choices=range(1, 11),
+                    help="multigrid workload: variables binned in every coordinate system")
+    ap.add_argument("--multigrid-res", type=int, default=256,
+                    help="multigrid workload: mesh side of every coordinate system")
+    ap.add_argument("--check", action="store_true",
+                    help="compare the last step with the CPU oracle and report per-bin errors")
+    ap.add_argument("--check-seconds", type=float, default=40.0,
+                    help="time budget of the batch workload's oracle check")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    n = args.n or WORKLOADS[args.workload][1]
+    if args.ops != "all":
+        args.check = False
+    standalone = {"batch256": run_batch, "serving": run_serving, "multigrid": run_multigrid}
+    if args.workload in standalone:
+        print(json.dumps(standalone[args.workload](args, n)), flush=True)
+        return 0
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    env = (rank, world, local, pg)
+    line = run_single(args, args.workload, n, env, with_e2e=True,
+                      with_cpu=not args.no_cpu_baseline, check=args.check)
+    headline_default = args.workload == "plummer1024" and not args.n and args.ops == "all"
+    if headline_default and not args.no_extras and world == 1:
+        # the other targets of the benchmark's metric, each measured on its
+        # own full-size workload with its own clocks record
+        sub = run_single(args, "uniform64_at_scale", WORKLOADS["uniform64_at_scale"][1], env,
+                         with_e2e=False, with_cpu=False, check=True, steps=50)
+        line["uniform64_at_scale"] = sub_object(sub)
+        bargs = argparse.Namespace(**vars(args))
+        bargs.steps, bargs.warmup, bargs.check, bargs.strategy = 5, 3, True, "auto"
+        line["batch256"] = run_batch(bargs, WORKLOADS["batch256"][1])
+        sargs = argparse.Namespace(**vars(args))
+        sargs.serving_priority, sargs.no_producer = "high", False
+        line["serving"] = run_serving(sargs, WORKLOADS["serving"][1])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0

@@ -406,33 +406,64 @@ BN_API bn_status bn_merge_results(bn_context* ctx, const bn_result* parts, int n
 BN_API bn_status bn_query(bn_request* req);
 
 /* Wait up to timeout_us microseconds (< 0: no limit). BN_ERR_TIMEOUT if the
- * request is still running; otherwise as bn_query. */
+ * request is still running; otherwise as bn_query. The blocking form of
+ * bn_query: the Synchronize() the paper's Listings 3 and 4 call before the
+ * host touches data produced on a device. */
 BN_API bn_status bn_wait(bn_request* req, int64_t timeout_us);
 
 /* Release a request: waits for completion if it is still running, runs the
- * deleters of the input handles it was given, frees its temporaries. */
+ * deleters of the input handles it was given (the coordinated life cycle of
+ * zero-copy buffers, Listing 1's shared_ptr deleter), frees its temporaries. */
 BN_API bn_status bn_request_release(bn_request* req);
 
-/* Free a library-allocated output (calls its deleter) and zero the handle.
- * A borrowed handle (no deleter) is only zeroed. */
+/* Free a library-allocated output (calls its deleter) and zero the handle
+ * (the shared_ptr deleter of Listing 1: the memory's life ends with its
+ * handle). Library outputs return to the stream-ordered pool on the stream
+ * that allocated them, after the work queued there, without synchronising
+ * the device; release them before destroying the context that made them. A
+ * borrowed handle (no deleter) is only zeroed. */
 BN_API bn_status bn_buffer_release(bn_buffer* buf);
 
 /* ----------------------------------------------------------------- serving */
 
 typedef struct bn_server_options {
     size_t budget_bytes;     /* device memory the server may hold for admitted
-                                requests: input copies + outputs + scratch */
+                                requests: input copies + temporaries (an upper
+                                bound of what each request's strategy may use) */
     int32_t max_inflight;    /* launches in flight at once (default 4) */
     int32_t max_batch;       /* requests merged into one launch (default 64) */
     int32_t stream_priority; /* of the server's streams (default: lowest) */
     int32_t reserved;
+    size_t staging_bytes;    /* page-locked host arena allocated once at
+                                creation for the deep copies of requests that
+                                do not fit the budget at submit time
+                                (0 = min(budget / 4, 4 GiB)) */
 } bn_server_options;
 
 typedef struct bn_server_stats {
     uint64_t submitted, admitted, completed, failed;
     uint64_t launches;
     size_t bytes_in_use, peak_bytes;
+    uint64_t staged;           /* deep copies placed in the staging arena */
+    uint64_t staging_overflow; /* deep copies that found the arena full and
+                                  took a page-locked allocation of their own */
+    uint64_t overdrawn;        /* requests whose temporaries exceeded what
+                                  admission charged (0 unless the accounting
+                                  is wrong) */
 } bn_server_stats;
+
+/* Where one server request's time went (host clock, microseconds). */
+typedef struct bn_request_timing {
+    double submit_us;    /* inside bn_server_submit: checks and the deep copy queued */
+    double queue_us;     /* submit returned -> admitted by the server */
+    double launch_us;    /* admitted -> its batch queued on a stream */
+    double complete_us;  /* batch queued -> completion seen by the server */
+    double batch_gpu_us; /* device time of its batch, events on the batch's stream
+                            (includes waiting for SMs held by other work) */
+    int32_t batch_size;  /* requests in its batch */
+    int32_t staged;      /* deep copy: 0 device memory, 1 staging arena,
+                            2 a page-locked allocation of its own */
+} bn_request_timing;
 
 /*
  * The asynchronous in situ method of Sec. 3: a server that deep-copies each
@@ -447,12 +478,19 @@ typedef struct bn_server_stats {
  */
 BN_API bn_status bn_server_create(bn_context* ctx, const bn_server_options* opt, bn_server** srv);
 
-/* Never blocks on the device: copies the block's columns into pinned staging
- * (host inputs) or device copies (device inputs), queues the request and
- * returns a request handle to poll or wait on. BN_ERR_BUDGET if the request
- * alone exceeds the budget. Outputs must be caller-allocated (device or
- * host) and must stay valid until the request completes. */
+/* Never blocks on the device: copies the block's columns into device memory
+ * when the budget has room (device inputs) or into the server's page-locked
+ * staging arena (host inputs, or no room yet; only when the arena is full
+ * does it allocate page-locked memory, which can take milliseconds), queues
+ * the request and returns a request handle to poll or wait on.
+ * BN_ERR_BUDGET if the request alone exceeds the budget. Outputs must be
+ * caller-allocated (device or host) and must stay valid until the request
+ * completes. */
 BN_API bn_status bn_server_submit(bn_server* srv, const bn_block* block, uint32_t ops, bn_request** req);
+
+/* The timing record of a completed server request (BN_NOT_READY while it
+ * runs; BN_ERR_INVALID_ARG for a request that did not come from a server). */
+BN_API bn_status bn_server_request_timing(bn_request* req, bn_request_timing* timing);
 
 BN_API bn_status bn_server_stats_get(bn_server* srv, bn_server_stats* stats);
 

@@ -12,6 +12,10 @@
  *             the current positions (computed on the first call when
  *             *acc_valid == 0, then kept up to date)
  *   stream    cudaStream_t the step is queued on
+ * Each force evaluation is queued as launches over chunks of 4096 source
+ * bodies, in order, so that no CTA of the producer holds an SM for a whole
+ * step: kernels of other streams (the binning server) get SMs between
+ * chunks. The j-order of the sums is the same as one launch's.
  * Errors: BN_ERR_INVALID_ARG for NULL pointers or n < 1, BN_ERR_CUDA.
  */
 #ifndef BINNING_HARNESS_H

@@ -65,6 +65,15 @@ int bno_bin_f32(int64_t n, const float* x, const float* y, int n_attrs,
                 const float* const* attrs, bno_grid* g, uint64_t* count, double* sum,
                 float* mn, float* mx, double* avg, double* bounds_out);
 
+/* All-core CPU baseline (binning_threaded.c): per-thread private meshes,
+ * then a merge; results as bno_bin_*. */
+int bno_bin_threaded_f64(int64_t n, const double* x, const double* y, int n_attrs,
+                         const double* const* attrs, bno_grid* g, int nthreads, uint64_t* count,
+                         double* sum, double* mn, double* mx, double* avg);
+int bno_bin_threaded_f32(int64_t n, const float* x, const float* y, int n_attrs,
+                         const float* const* attrs, bno_grid* g, int nthreads, uint64_t* count,
+                         double* sum, float* mn, float* mx, double* avg);
+
 int bno_particle_bin_f64(double x, double y, const double* lo, const double* hi,
                          const double* s, const int32_t* res, int closed, int32_t* ixy);
 int bno_particle_bin_f32(float x, float y, const double* lo, const double* hi,

@@ -25,7 +25,7 @@ from ._abi import (CTX_PROFILE, ALLOC_CUDA_ASYNC, ALLOC_EXTERNAL, ALLOC_HOST, AL
                    AGG_AUTO, AGG_ON, AGG_OFF, AGG_MASK,
                    MAX_MULTI_COLS, MAX_MULTI_SPECS,
                    bn_block, bn_buffer, bn_grid, bn_grid_spec, bn_options, bn_result,
-                   bn_server_options, bn_server_stats)
+                   bn_server_options, bn_server_stats, bn_request_timing)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libbinning.so")
@@ -261,9 +261,10 @@ def bn_request_release(req: int) -> None:
 
 
 def bn_server_create(ctx: int, budget_bytes: int, max_inflight: int = 4, max_batch: int = 64,
-                     priority: int = 0) -> int:
+                     priority: int = 0, staging_bytes: int = 0) -> int:
     o = bn_server_options()
     o.budget_bytes = budget_bytes
+    o.staging_bytes = staging_bytes
     o.max_inflight = max_inflight
     o.max_batch = max_batch
     o.stream_priority = priority
@@ -276,6 +277,16 @@ def bn_server_submit(srv: int, block: bn_block, ops: int) -> int:
     req = ctypes.c_void_p()
     check(lib().bn_server_submit(srv, ctypes.byref(block), ops, ctypes.byref(req)))
     return req.value
+
+
+def bn_server_request_timing(req: int) -> Optional[Dict[str, float]]:
+    """Timing record of a completed server request (None while it runs)."""
+    t = bn_request_timing()
+    st = lib().bn_server_request_timing(req, ctypes.byref(t))
+    if st == NOT_READY:
+        return None
+    check(st)
+    return {k: getattr(t, k) for k, _ in bn_request_timing._fields_}
 
 
 def bn_server_stats_get(srv: int) -> Dict[str, int]:

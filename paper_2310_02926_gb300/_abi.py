@@ -101,14 +101,22 @@ class bn_options(ctypes.Structure):
 class bn_server_options(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("stream_priority", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("staging_bytes", ctypes.c_size_t)]
 
 
 class bn_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
                 ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
                 ("launches", ctypes.c_uint64), ("bytes_in_use", ctypes.c_size_t),
-                ("peak_bytes", ctypes.c_size_t)]
+                ("peak_bytes", ctypes.c_size_t), ("staged", ctypes.c_uint64),
+                ("staging_overflow", ctypes.c_uint64), ("overdrawn", ctypes.c_uint64)]
+
+
+class bn_request_timing(ctypes.Structure):
+    _fields_ = [("submit_us", ctypes.c_double), ("queue_us", ctypes.c_double),
+                ("launch_us", ctypes.c_double), ("complete_us", ctypes.c_double),
+                ("batch_gpu_us", ctypes.c_double), ("batch_size", ctypes.c_int32),
+                ("staged", ctypes.c_int32)]
 
 
 P = ctypes.c_void_p
@@ -145,6 +153,7 @@ PROTOTYPES = {
     "bn_server_create": (S, [P, ctypes.POINTER(bn_server_options), PP]),
     "bn_server_submit": (S, [P, ctypes.POINTER(bn_block), ctypes.c_uint32, PP]),
     "bn_server_stats_get": (S, [P, ctypes.POINTER(bn_server_stats)]),
+    "bn_server_request_timing": (S, [P, ctypes.POINTER(bn_request_timing)]),
     "bn_server_destroy": (S, [P]),
     "bn_nbody_step": (S, [P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.c_int64, ctypes.c_float,
                           ctypes.c_float, P]),

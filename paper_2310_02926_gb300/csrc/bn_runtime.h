@@ -93,6 +93,7 @@ struct Plan {
     std::vector<Copy> d2h;
     cudaError_t err = cudaSuccess;
     size_t h2d_bytes = 0, d2h_bytes = 0;
+    size_t temp_bytes = 0;  // bytes of every temporary alloc() handed out
     int strategy = 0;
     // false: an unseen shape class takes the heuristic strategy instead of
     // timing the candidates (the trials synchronise with the device; a
@@ -120,6 +121,7 @@ bn_status enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const bn_bu
                       const bn_buffer* attrs, int n_attrs, const bn_grid* grid, uint32_t ops,
                       bn_result* out, int* status_dev);
 bn_status complete_sync(bn_request* r, int sync, bn_request** req);
+size_t request_temp_bytes(const bn_context* c, const bn_block& b, int dtype, uint32_t ops);
 void batch_cache_release(bn_context* c);
 
 }  // namespace bn

@@ -9,18 +9,34 @@
 namespace {
 
 constexpr int kTile = 256;
+// Bodies j one launch of the force kernel sums over. One launch over all
+// bodies keeps every CTA resident for the whole step (about 2.7 ms at
+// N = 65,536), and a kernel of another stream that needs a whole SM (a
+// binning request of the server) waits for those CTAs to finish; chunks of
+// 4096 end every CTA after about 0.2 ms. The chunks run in order on the
+// producer's stream, each adding to the previous one's sums, so the result
+// does not depend on how the launches interleave with other work.
+constexpr int64_t kChunk = 4096;
 
-// Accelerations of all bodies: each thread owns one body, the block walks
-// the bodies in shared-memory tiles of kTile.
+// Accelerations from bodies [j_begin, j_end): each thread owns one body, the
+// block walks those bodies in shared-memory tiles of kTile; the first chunk
+// writes acc, later chunks add to it.
 __global__ void __launch_bounds__(kTile) k_nbody_acc(const float4* __restrict__ pos,
-                                                     float4* __restrict__ acc, int64_t n, float eps2) {
+                                                     float4* __restrict__ acc, int64_t n, float eps2,
+                                                     int64_t j_begin, int64_t j_end) {
     __shared__ float4 tile[kTile];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const float4 pi = i < n ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     float ax = 0.f, ay = 0.f, az = 0.f;
-    for (int64_t j0 = 0; j0 < n; j0 += kTile) {
+    if (j_begin > 0 && i < n) {
+        const float4 a = acc[i];
+        ax = a.x;
+        ay = a.y;
+        az = a.z;
+    }
+    for (int64_t j0 = j_begin; j0 < j_end; j0 += kTile) {
         const int64_t j = j0 + threadIdx.x;
-        tile[threadIdx.x] = j < n ? pos[j] : make_float4(0.f, 0.f, 0.f, 0.f);  // w = 0: no pull
+        tile[threadIdx.x] = j < j_end ? pos[j] : make_float4(0.f, 0.f, 0.f, 0.f);  // w = 0: no pull
         __syncthreads();
 #pragma unroll 8
         for (int k = 0; k < kTile; ++k) {
@@ -80,12 +96,16 @@ extern "C" bn_status bn_nbody_step(void* pos, void* vel, void* acc, int* acc_val
     float4* V = static_cast<float4*>(vel);
     float4* A = static_cast<float4*>(acc);
     const float eps2 = eps * eps;
+    auto forces = [&]() {
+        for (int64_t j = 0; j < n; j += kChunk)
+            k_nbody_acc<<<grid, kTile, 0, s>>>(P, A, n, eps2, j, j + kChunk < n ? j + kChunk : n);
+    };
     if (!*acc_valid) {
-        k_nbody_acc<<<grid, kTile, 0, s>>>(P, A, n, eps2);
+        forces();
         *acc_valid = 1;
     }
     k_nbody_kick_drift<<<grid, kTile, 0, s>>>(P, V, A, n, dt);
-    k_nbody_acc<<<grid, kTile, 0, s>>>(P, A, n, eps2);
+    forces();
     k_nbody_kick<<<grid, kTile, 0, s>>>(V, A, n, dt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bn::cuda_fail(e, "bn_nbody_step");

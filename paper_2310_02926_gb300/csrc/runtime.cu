@@ -298,9 +298,11 @@ extern "C" bn_status bn_request_release(bn_request* r) {
     return BN_OK;
 }
 
+// Library outputs return to the stream-ordered pool on the stream that
+// allocated them (ctx): no device-wide synchronisation, and ordered after
+// every kernel the library queued there.
 static void lib_free_deleter(void* ptr, void* ctx) {
-    (void)ctx;
-    if (ptr) cudaFree(ptr);  // memory from cudaMallocAsync may be freed with cudaFree
+    if (ptr) cudaFreeAsync(ptr, static_cast<cudaStream_t>(ctx));
 }
 
 extern "C" bn_status bn_buffer_release(bn_buffer* b) {
@@ -380,12 +382,14 @@ bn_status bn::make_grid_desc(const bn_grid* g, int dtype, GridDesc* out) {
 void* Plan::alloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
     void* p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, (bytes + 255) & ~(size_t)255, stream);
+    const size_t rounded = (bytes + 255) & ~(size_t)255;
+    cudaError_t e = cudaMallocAsync(&p, rounded, stream);
     if (e != cudaSuccess) {
         err = e;
         return nullptr;
     }
     temps.push_back(p);
+    temp_bytes += rounded;
     return p;
 }
 
@@ -508,7 +512,7 @@ bn_status Plan::output(bn_buffer* b, bool wanted, int64_t bins, int dtype, bool 
         b->stream = stream;
         b->alloc = BN_ALLOC_CUDA_ASYNC;
         b->deleter = lib_free_deleter;
-        b->deleter_ctx = nullptr;
+        b->deleter_ctx = stream;
         *out = p;
         return BN_OK;
     }
@@ -572,6 +576,55 @@ int bn::choose_strategy(const BinArgs& a, int smem_optin, int num_sms, uint32_t 
         a.n >= (int64_t)num_sms * sd.tp && a.n >= B / 4)
         return BN_STRATEGY_SORT;
     return BN_STRATEGY_GLOBAL;
+}
+
+// An upper bound on the device temporaries enqueue_bin allocates for one
+// block (the server charges it to its budget before admitting the block):
+// state the caller did not ask for, device copies of host outputs, min/max
+// key records and their filter, the sort path's scratch whenever the mesh
+// has a sort plan, the mesh descriptor, edge keys and bounds accumulator.
+// The block's columns are taken as contiguous device data.
+size_t bn::request_temp_bytes(const bn_context* c, const bn_block& b, int dtype, uint32_t ops) {
+    auto r256 = [](size_t v) { return (std::max(v, (size_t)16) + 255) & ~(size_t)255; };
+    const size_t es = dtype_size(dtype);
+    const int64_t B = (int64_t)b.grid.res[0] * b.grid.res[1];
+    const bool want_avg = ops & BN_OP_AVG, want_sum = ops & BN_OP_SUM;
+    const bool want_min = ops & BN_OP_MIN, want_max = ops & BN_OP_MAX, want_count = ops & BN_OP_COUNT;
+    const int A = (want_sum || want_avg || want_min || want_max) ? b.n_attrs : 0;
+    const bn_result* o = b.out;
+    auto host_or_missing = [&](const bn_buffer& buf, bool wanted) {
+        return !wanted || !buf.ptr || buf.device == BN_HOST;
+    };
+    size_t t = 0;
+    if (host_or_missing(o->count, want_count)) t += r256((size_t)B * 8);
+    for (int a = 0; a < A; ++a) {
+        if ((want_sum || want_avg) && host_or_missing(o->sum[a], want_sum)) t += r256((size_t)B * 8);
+        if (want_min && o->min[a].device == BN_HOST) t += r256((size_t)B * es);
+        if (want_max && o->max[a].device == BN_HOST) t += r256((size_t)B * es);
+        if (want_avg && o->avg[a].device == BN_HOST) t += r256((size_t)B * 8);
+    }
+    if (A > 0 && (want_min || want_max)) {
+        t += r256((size_t)key_record_pairs(A, (int)es) * B * 2 * es);
+        if (dtype == BN_F64 && A >= 3) t += r256((size_t)filter_record_pairs(A) * B * sizeof(int2));
+    }
+    BinArgs a;
+    memset(&a, 0, sizeof a);
+    a.dtype = dtype;
+    a.n_attrs = A;
+    a.n = b.x.n;
+    a.sum_mode = dtype == BN_F64 ? kSumF64 : (ops & BN_SUM_MASK) == BN_SUM_F32 ? kSumF32
+                                           : (ops & BN_SUM_MASK) == BN_SUM_F64 ? kSumF64 : kSumF32C;
+    a.grid.ax[0].res = b.grid.res[0];
+    a.grid.ax[1].res = b.grid.res[1];
+    a.st.do_sum = (want_sum || want_avg) ? 1 : 0;
+    a.st.do_min = want_min;
+    a.st.do_max = want_max;
+    SortDesc sd;
+    if (sort_plan(a, c->smem_optin, &sd)) t += r256(sort_scratch_bytes(sd, a));
+    t += r256(sizeof(GridDesc)) + r256(4 * es);
+    if (dtype == BN_F64) t += r256(8 * ((size_t)b.grid.res[0] + 1)) + r256(8 * ((size_t)b.grid.res[1] + 1));
+    if (o->bounds.ptr && o->bounds.device == BN_HOST) t += r256(4 * 8);
+    return t;
 }
 
 bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const bn_buffer* y,

@@ -5,8 +5,9 @@
 // data it needs, hands the work to a thread and returns to the simulation at
 // once; simulation and analysis then run concurrently. Here:
 //   submit   deep-copies the block's columns (device data: a device copy if
-//            the memory budget has room now, otherwise a pinned host copy;
-//            host data: a pinned host copy), makes each input's owning
+//            the memory budget has room now, otherwise a copy into the
+//            page-locked staging arena the server allocated at creation;
+//            host data: a staging-arena copy), makes each input's owning
 //            stream wait for the copy (so the caller may overwrite its
 //            buffers with any later work on that stream), queues the
 //            request and returns a handle;
@@ -28,6 +29,8 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <iterator>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -38,6 +41,53 @@
 using namespace bn;
 
 namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double us_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::micro>(b - a).count();
+}
+
+// Page-locked host memory allocated once, handed out first-fit in 256-byte
+// units: submit never has to page-lock memory on the request path.
+struct Arena {
+    char* base = nullptr;
+    size_t size = 0;
+    std::mutex mu;
+    std::map<size_t, size_t> free_;  // offset -> bytes, adjacent runs merged
+
+    static size_t round(size_t n) { return (std::max(n, (size_t)1) + 255) & ~(size_t)255; }
+    bool alloc(size_t n, size_t* off) {
+        n = round(n);
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            *off = it->first;
+            const size_t rest = it->second - n, o2 = it->first + n;
+            free_.erase(it);
+            if (rest) free_[o2] = rest;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        n = round(n);
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
 
 struct Job {
     bn_request* req = nullptr;
@@ -51,12 +101,20 @@ struct Job {
     size_t need = 0;          // device bytes charged to the budget
     bool on_device = false;   // inputs already copied to device memory
     void* dev_copy = nullptr; // device copy of all columns (one allocation)
-    void* host_copy = nullptr;// pinned host staging (when not on device)
+    void* host_copy = nullptr;// page-locked staging (when not on device)
+    int staged = 0;           // 0 device copy, 1 staging arena, 2 own page-locked allocation
+    size_t arena_off = 0;
+    size_t copy_bytes = 0;
     cudaEvent_t copied = nullptr;
+    // timing record (bn_request_timing)
+    Clock::time_point t_submit0, t_submit1, t_admit, t_launch, t_done;
+    double batch_gpu_us = 0.0;
+    int batch_size = 0;
 };
 
 struct Slot {
     cudaStream_t stream = nullptr;
+    cudaEvent_t start = nullptr;
     cudaEvent_t done = nullptr;
     std::vector<Job*> jobs;
     bool busy = false;
@@ -76,28 +134,29 @@ struct bn_server {
     std::deque<Job*> queue;  // submitted, waiting for admission
     bool stop = false;
     size_t in_use = 0, peak = 0;
+    Arena arena;
     std::atomic<uint64_t> submitted{0}, admitted{0}, completed{0}, failed{0}, launches{0};
+    std::atomic<uint64_t> staged{0}, staging_overflow{0}, overdrawn{0};
 };
-
-static size_t state_bytes(const bn_block& b, int dtype, uint32_t ops) {
-    // temporaries the library may need for state the caller did not ask for
-    // (count, sums for avg) plus grid descriptor and f64 edge tables
-    const size_t B = (size_t)b.grid.res[0] * b.grid.res[1];
-    size_t s = B * 8 + (size_t)b.n_attrs * B * 8 + 4096;
-    if (dtype == BN_F64) s += 8 * ((size_t)b.grid.res[0] + b.grid.res[1] + 2);
-    (void)ops;
-    return s;
-}
 
 static void job_release_hook(bn_request* r) {
     Job* j = static_cast<Job*>(r->owner);
     if (!j) return;
-    if (j->host_copy) cudaFreeHost(j->host_copy);
+    if (j->host_copy && j->staged == 2) cudaFreeHost(j->host_copy);
     if (j->copied) r->ctx->put_event(j->copied);
     delete j;
 }
 
 static void finish_job(bn_server* s, Job* j, int st) {
+    j->t_done = Clock::now();
+    // the batch is complete, so its host-to-device copy is too: the staging
+    // space can take the next request (a job that failed before launch may
+    // still have its copy queued)
+    if (j->host_copy && j->staged == 1) {
+        if (st < 0) cudaStreamSynchronize(s->copy_stream);
+        s->arena.release(j->arena_off, j->copy_bytes);
+        j->host_copy = nullptr;
+    }
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->in_use -= j->need;
@@ -114,11 +173,14 @@ static void launch_batch(bn_server* s, Slot& slot, std::vector<Job*>& batch) {
     std::lock_guard<std::mutex> lk(c->enqueue_mu);
     Plan plan(c, slot.stream);
     plan.may_tune = false;  // shape classes the context has tuned keep their choice
+    cudaEventRecord(slot.start, slot.stream);
     for (Job* j : batch) {
         if (j->copied) cudaStreamWaitEvent(slot.stream, j->copied, 0);
+        const size_t before = plan.temp_bytes;
         bn_status st = enqueue_bin(c, plan, &j->block.x, &j->block.y, j->block.attrs,
                                    j->block.n_attrs, &j->block.grid, j->ops, &j->out,
                                    c->status_dev + j->req->slot);
+        if (plan.temp_bytes - before > j->need - j->copy_bytes) s->overdrawn++;
         if (st != BN_OK) {
             j->req->host_status = st;
             j->status.store(st, std::memory_order_release);
@@ -139,6 +201,11 @@ static void launch_batch(bn_server* s, Slot& slot, std::vector<Job*>& batch) {
         if (static_cast<cudaStream_t>(os) != slot.stream)
             cudaStreamWaitEvent(static_cast<cudaStream_t>(os), slot.done, 0);
     s->launches++;
+    const Clock::time_point now = Clock::now();
+    for (Job* j : batch) {
+        j->t_launch = now;
+        j->batch_size = (int)batch.size();
+    }
     slot.jobs = batch;
     slot.busy = true;
 }
@@ -151,7 +218,10 @@ static void worker_main(bn_server* s) {
             if (!sl.busy) continue;
             cudaError_t e = cudaEventQuery(sl.done);
             if (e == cudaErrorNotReady) continue;
+            float gpu_ms = 0.0f;
+            if (e == cudaSuccess && cudaEventElapsedTime(&gpu_ms, sl.start, sl.done) != cudaSuccess) gpu_ms = 0.0f;
             for (Job* j : sl.jobs) {
+                j->batch_gpu_us = 1e3 * (double)gpu_ms;
                 int st = j->status.load(std::memory_order_acquire);
                 if (st == BN_NOT_READY) {
                     st = e == cudaSuccess ? s->ctx->status_host[j->req->slot] : BN_ERR_CUDA;
@@ -191,8 +261,10 @@ static void worker_main(bn_server* s) {
             }
         }
         // move pinned-staged inputs to the device
+        const Clock::time_point t_admit = Clock::now();
         for (Job* j : batch) {
             s->admitted++;
+            j->t_admit = t_admit;
             if (j->on_device) continue;
             void* d = nullptr;
             size_t bytes = j->col_bytes * (2 + j->block.n_attrs);
@@ -239,14 +311,30 @@ extern "C" bn_status bn_server_create(bn_context* c, const bn_server_options* op
     cudaError_t e = cudaStreamCreateWithPriority(&s->copy_stream, cudaStreamNonBlocking, prio);
     for (Slot& sl : s->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, prio);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreate(&sl.start);  // timed: batch_gpu_us
+        if (e == cudaSuccess) e = cudaEventCreate(&sl.done);
+    }
+    // the staging arena: page-locked once, here, not per request
+    size_t staging = (opt && opt->staging_bytes) ? opt->staging_bytes
+                                                 : std::min(s->budget / 4, (size_t)4 << 30);
+    staging = (staging + 255) & ~(size_t)255;
+    if (e == cudaSuccess && staging) {
+        void* base = nullptr;
+        e = cudaHostAlloc(&base, staging, cudaHostAllocDefault);
+        if (e == cudaSuccess) {
+            s->arena.base = static_cast<char*>(base);
+            s->arena.size = staging;
+            s->arena.free_[0] = staging;
+        }
     }
     if (e != cudaSuccess) {
         for (Slot& sl : s->slots) {
             if (sl.stream) cudaStreamDestroy(sl.stream);
+            if (sl.start) cudaEventDestroy(sl.start);
             if (sl.done) cudaEventDestroy(sl.done);
         }
         if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+        if (s->arena.base) cudaFreeHost(s->arena.base);
         delete s;
         return cuda_fail(e, "bn_server_create");
     }
@@ -256,6 +344,7 @@ extern "C" bn_status bn_server_create(bn_context* c, const bn_server_options* op
 }
 
 extern "C" bn_status bn_server_submit(bn_server* s, const bn_block* b, uint32_t ops, bn_request** req) {
+    const Clock::time_point t0 = Clock::now();
     if (!s || !b || !req) return fail(BN_ERR_INVALID_ARG, "bn_server_submit: NULL argument");
     *req = nullptr;
     bn_context* c = s->ctx;
@@ -292,9 +381,11 @@ extern "C" bn_status bn_server_submit(bn_server* s, const bn_block* b, uint32_t 
     j->ops = ops & ~(uint32_t)BN_OP_ACCUMULATE;
     j->dtype = dtype;
     j->n = n;
+    j->t_submit0 = t0;
     j->col_bytes = ((size_t)n * es + 255) & ~(size_t)255;
     const size_t copy_bytes = j->col_bytes * (2 + b->n_attrs);
-    j->need = copy_bytes + state_bytes(*b, dtype, ops);
+    j->copy_bytes = copy_bytes;
+    j->need = copy_bytes + request_temp_bytes(c, *b, dtype, j->ops);
     if (j->need > s->budget) {
         delete j;
         return fail(BN_ERR_BUDGET, "bn_server_submit: request needs %zu bytes, budget is %zu", j->need, s->budget);
@@ -316,8 +407,11 @@ extern "C" bn_status bn_server_submit(bn_server* s, const bn_block* b, uint32_t 
     for (int a = 0; a < b->n_attrs; ++a) all_dev = all_dev && b->attrs[a].device != BN_HOST;
     bool charged = false;
     if (all_dev) {
+        // a device copy whenever the budget has room, even behind a queue:
+        // staging through host memory while a backlog drains would slow
+        // every later request and feed the backlog
         std::lock_guard<std::mutex> lk(s->mu);
-        if (s->queue.empty() && s->in_use + j->need <= s->budget) {
+        if (s->in_use + j->need <= s->budget) {
             s->in_use += j->need;
             s->peak = std::max(s->peak, s->in_use);
             charged = true;
@@ -340,8 +434,20 @@ extern "C" bn_status bn_server_submit(bn_server* s, const bn_block* b, uint32_t 
     }
     void* dst = nullptr;
     if (e == cudaSuccess) {
-        if (charged) e = cudaMallocAsync(&dst, copy_bytes ? copy_bytes : 16, s->copy_stream);
-        else e = cudaHostAlloc(&dst, copy_bytes ? copy_bytes : 16, cudaHostAllocDefault);
+        if (charged) {
+            e = cudaMallocAsync(&dst, copy_bytes ? copy_bytes : 16, s->copy_stream);
+        } else if (s->arena.base && s->arena.alloc(copy_bytes, &j->arena_off)) {
+            // earlier copies into the same arena range were consumed by
+            // batches that completed before the range was released
+            dst = s->arena.base + j->arena_off;
+            j->staged = 1;
+            s->staged++;
+        } else {
+            // the arena is full or too small: page-lock memory for this one
+            e = cudaHostAlloc(&dst, copy_bytes ? copy_bytes : 16, cudaHostAllocDefault);
+            j->staged = 2;
+            s->staging_overflow++;
+        }
     }
     for (int k = 0; k < ncol && e == cudaSuccess && n > 0; ++k) {
         const bn_buffer* col = cols[k];
@@ -370,6 +476,12 @@ extern "C" bn_status bn_server_submit(bn_server* s, const bn_block* b, uint32_t 
             std::lock_guard<std::mutex> lk(s->mu);
             s->in_use -= j->need;
         }
+        if (dst && !charged) {
+            cudaStreamSynchronize(s->copy_stream);  // copies already queued from it
+            if (j->staged == 1) s->arena.release(j->arena_off, copy_bytes);
+            else cudaFreeHost(dst);
+        }
+        j->staged = 0;
         j->status.store(BN_ERR_CUDA);
         r->host_status = BN_ERR_CUDA;
         bn_status out = cuda_fail(e, "bn_server_submit: deep copy");
@@ -403,6 +515,7 @@ extern "C" bn_status bn_server_submit(bn_server* s, const bn_block* b, uint32_t 
     // stream, which the worker's slot stream waits on through `copied`
     j->block.x.stream = j->block.y.stream = s->copy_stream;
     for (int a = 0; a < b->n_attrs; ++a) j->block.attrs[a].stream = s->copy_stream;
+    j->t_submit1 = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->queue.push_back(j);
@@ -423,6 +536,25 @@ extern "C" bn_status bn_server_stats_get(bn_server* s, bn_server_stats* out) {
     out->launches = s->launches.load();
     out->bytes_in_use = s->in_use;
     out->peak_bytes = s->peak;
+    out->staged = s->staged.load();
+    out->staging_overflow = s->staging_overflow.load();
+    out->overdrawn = s->overdrawn.load();
+    return BN_OK;
+}
+
+extern "C" bn_status bn_server_request_timing(bn_request* r, bn_request_timing* out) {
+    if (!r || !out || r->on_release != job_release_hook || !r->owner)
+        return fail(BN_ERR_INVALID_ARG, "bn_server_request_timing: not a server request");
+    const Job* j = static_cast<const Job*>(r->owner);
+    if (j->status.load(std::memory_order_acquire) == BN_NOT_READY) return BN_NOT_READY;
+    memset(out, 0, sizeof *out);
+    out->submit_us = us_between(j->t_submit0, j->t_submit1);
+    out->queue_us = us_between(j->t_submit1, j->t_admit);
+    out->launch_us = j->batch_size ? us_between(j->t_admit, j->t_launch) : 0.0;
+    out->complete_us = j->batch_size ? us_between(j->t_launch, j->t_done) : 0.0;
+    out->batch_gpu_us = j->batch_gpu_us;
+    out->batch_size = j->batch_size;
+    out->staged = j->staged;
     return BN_OK;
 }
 
@@ -438,10 +570,13 @@ extern "C" bn_status bn_server_destroy(bn_server* s) {
     for (Slot& sl : s->slots) {
         cudaStreamSynchronize(sl.stream);
         cudaStreamDestroy(sl.stream);
+        cudaEventDestroy(sl.start);
         cudaEventDestroy(sl.done);
     }
     cudaStreamSynchronize(s->copy_stream);
     cudaStreamDestroy(s->copy_stream);
+    // every request has finished, so no arena range is in use any more
+    if (s->arena.base) cudaFreeHost(s->arena.base);
     delete s;
     return BN_OK;
 }

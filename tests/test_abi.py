@@ -36,7 +36,7 @@ def test_struct_layouts_match_header(bn, tmp_path):
     from paper_2310_02926_gb300 import _abi
     src = tmp_path / "sz.c"
     structs = ["bn_buffer", "bn_grid", "bn_result", "bn_block", "bn_grid_spec", "bn_options",
-               "bn_server_options", "bn_server_stats"]
+               "bn_server_options", "bn_server_stats", "bn_request_timing"]
     body = "\n".join(f'printf("%zu\\n", sizeof({s}));' for s in structs)
     offs = [("bn_buffer", "stream"), ("bn_buffer", "deleter"), ("bn_block", "grid"),
             ("bn_grid_spec", "grid"),

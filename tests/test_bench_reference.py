@@ -26,3 +26,5 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
     assert d["config"]["name"] == "plummer1024"
+    assert d["config"]["sample_particles_per_step"] == 20000
+    assert "l2" not in d["config"]

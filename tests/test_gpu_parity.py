@@ -656,22 +656,26 @@ def test_server_does_not_run_autotuner_trials(bn):
     fresh.close()
 
 
-@pytest.mark.parametrize("inputs", ["host", "device_tight_budget", "strided"])
+@pytest.mark.parametrize("inputs", ["host", "device_tight_budget", "strided", "arena_overflow"])
 def test_server_staging_paths(bn, ctx, inputs):
-    """Requests whose columns are on the host, or that arrive while the budget
-    is used up (deep copy to pinned host memory, admitted later), or whose
-    columns are strided: every result equals binning the block alone."""
+    """Requests whose columns are on the host (deep copy into the staging
+    arena), or that arrive while the budget is used up (staged, admitted
+    later), or whose columns are strided, or that find the staging arena
+    full (a page-locked allocation of their own): every result equals
+    binning the block alone, and the admission charge covers every
+    request's temporaries."""
     rng = np.random.default_rng(61)
     n_req = 12
     sizes = rng.integers(20_000, 120_000, n_req)
     side = 48
     budget = 6 << 20 if inputs == "device_tight_budget" else 1 << 30
-    srv = bn.bn_server_create(ctx.handle, budget, max_inflight=2, max_batch=3)
+    staging = 1 << 20 if inputs == "arena_overflow" else 0
+    srv = bn.bn_server_create(ctx.handle, budget, max_inflight=2, max_batch=3, staging_bytes=staging)
     reqs = []
     for i in range(n_req):
         w = workloads.plummer(int(sizes[i]), seed=100 + i, dtype=np.float32, res=side)
         w.attrs[2] = np.abs(w.attrs[2])
-        if inputs == "host":
+        if inputs in ("host", "arena_overflow"):
             cols = [torch.from_numpy(c) for c in (w.x, w.y, *w.attrs)]
         elif inputs == "strided":
             aos = torch.from_numpy(np.stack([w.x, w.y, *w.attrs], axis=1)).cuda()
@@ -684,14 +688,94 @@ def test_server_staging_paths(bn, ctx, inputs):
         reqs.append((bn.bn_server_submit(srv, blk, bn.OP_ALL), o, r, blk, cols, w))
     for req, *_ in reqs:
         assert bn.bn_wait(req, 60_000_000) == bn.OK
+        t = bn.bn_server_request_timing(req)
+        assert t is not None and t["batch_size"] >= 1 and t["submit_us"] >= 0 and t["batch_gpu_us"] > 0
         bn.bn_request_release(req)
     stats = bn.bn_server_stats_get(srv)
     bn.bn_server_destroy(srv)
     assert stats["completed"] == n_req and stats["failed"] == 0
+    assert stats["overdrawn"] == 0
     if inputs == "device_tight_budget":
         assert stats["peak_bytes"] <= budget
+    if inputs == "host":
+        assert stats["staged"] == n_req and stats["staging_overflow"] == 0
+    if inputs == "arena_overflow":
+        assert stats["staging_overflow"] > 0
     for req, o, r, blk, cols, w in reqs:
         check(w, to_numpy_result(o), TOL_F32C, label=f"{inputs} {w.n}")
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_server_charges_cover_temporaries(bn, dtype):
+    """Requests of every strategy and shape class (min/max key records and
+    their f64 filter, sort scratch, host outputs, avg without sum) through
+    one server: what each request's plan allocates never exceeds what
+    admission charged it, and every result matches the oracle."""
+    c = bn.Context(0)
+    srv = bn.bn_server_create(c.handle, 8 << 30, max_inflight=3, max_batch=4)
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    cases = [  # (n, side, n_attrs, flags, ops, host outputs)
+        (300_000, 1024, 3, bn.STRATEGY_GLOBAL, bn.OP_ALL, False),
+        (400_000, 2048, 2, bn.STRATEGY_SORT, bn.OP_ALL, False),
+        (200_000, 512, 3, bn.STRATEGY_HYBRID, bn.OP_ALL, False),
+        (200_000, 40, 3, bn.STRATEGY_PRIVATE, bn.OP_ALL, False),
+        (150_000, 700, 3, 0, bn.OP_COUNT | bn.OP_AVG | bn.OP_MIN, False),
+        (150_000, 300, 2, 0, bn.OP_ALL, True),
+    ]
+    reqs = []
+    try:
+        for k, (n, side, A, flags, ops, host) in enumerate(cases):
+            w = workloads.plummer(n, seed=500 + k, dtype=dtype, res=side, n_attrs=A)
+            cols = [torch.from_numpy(x).cuda() for x in (w.x, w.y, *w.attrs)]
+            dev = torch.device("cpu") if host else torch.device("cuda")
+            o = bn.alloc_outputs(A, side * side, tdt, dev, ops=ops)
+            if host:
+                o = {kk: ([t.pin_memory() for t in v] if isinstance(v, list) else v.pin_memory())
+                     for kk, v in o.items()}
+            r = bn.result_struct(o)
+            blk = bn.block(cols[0], cols[1], cols[2:], bn.grid(w.lo, w.hi, w.res), r)
+            reqs.append((bn.bn_server_submit(srv, blk, ops | flags), o, r, blk, cols, w, ops))
+        for req, *_ in reqs:
+            assert bn.bn_wait(req, 120_000_000) == bn.OK
+            bn.bn_request_release(req)
+        stats = bn.bn_server_stats_get(srv)
+    finally:
+        bn.bn_server_destroy(srv)
+        c.close()
+    assert stats["failed"] == 0 and stats["overdrawn"] == 0
+    assert stats["peak_bytes"] <= 8 << 30
+    tol = TOL_F64 if dtype == np.float64 else TOL_F32C
+    for req, o, r, blk, cols, w, ops in reqs:
+        got = to_numpy_result(o)
+        ref = oracle.bin_workload(w)
+        keys = [k for k in ("count", "sum", "min", "max", "avg") if k in got]
+        assert_parity(got, ref, abs_sums(w), tol, check=keys, label=f"{w.n} {w.res}")
+
+
+def test_nbody_producer_forces_match_float64_reference(bn):
+    """The serving benchmark's producer (harness, not binning): after one
+    step, the accelerations it keeps equal the direct sum over all pairs
+    evaluated in float64 by plain torch, for a body count that spans two
+    force chunks and a ragged tail."""
+    import ctypes
+    g = torch.Generator().manual_seed(3)
+    n, eps = 5_003, 1e-2
+    pos = torch.zeros(n, 4)
+    pos[:, :3] = torch.randn(n, 3, generator=g)
+    pos[:, 3] = torch.rand(n, generator=g) / n
+    vel = torch.zeros(n, 4)
+    dp, dv, da = pos.cuda(), vel.cuda(), torch.zeros(n, 4, device="cuda")
+    ok = ctypes.c_int(0)
+    bn.bn_nbody_step(dp, dv, da, ok, 0.0, eps)  # dt = 0: positions stay, forces of pos
+    torch.cuda.synchronize()
+    p = pos.double()
+    got = da[:, :3].double().cpu()
+    for i0 in range(0, n, 500):  # rows in blocks: the pair arrays stay small
+        d = p[None, :, :3] - p[i0:i0 + 500, None, :3]
+        r2 = (d ** 2).sum(-1) + eps * eps
+        ref = (d * (p[None, :, 3] / r2 ** 1.5)[..., None]).sum(1)
+        scale = (p[None, :, 3] / r2).sum(1)[:, None]  # sum of |term| bounds
+        assert ((got[i0:i0 + 500] - ref).abs() <= 1e-4 * scale).all(), i0
 
 
 def test_server_rejects_over_budget(bn, ctx):

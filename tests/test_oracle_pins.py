@@ -420,3 +420,36 @@ def test_shard_merge_keeps_both_compensation_terms():
     assert r["sum"][0][0] == math.fsum([1e16, 1.0, -1e16, 1.0]) == 2.0
     assert r["count"][0] == 4
 
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("threads", [1, 3, 16])
+def test_threaded_baseline_equals_oracle(dtype, threads):
+    """The all-core CPU baseline (per-thread meshes, then a merge) gives the
+    single-threaded oracle's counts, min and max exactly and its sums to
+    within the reordering of Neumaier partial sums; automatic bounds and
+    NaN attributes included."""
+    w = workloads.plummer(200_003, seed=5, dtype=dtype, res=96)
+    w.attrs[1][::37] = np.nan
+    for auto in (False, True):
+        ref = oracle.bin_workload(w, auto)
+        got = oracle.bin_particles_threaded(w.x, w.y, w.attrs, w.lo, w.hi, w.res, auto, threads=threads)
+        np.testing.assert_array_equal(got["count"], ref["count"])
+        for k in ("min", "max"):
+            np.testing.assert_array_equal(got[k].view(np.int64 if dtype == np.float64 else np.int32),
+                                          ref[k].view(np.int64 if dtype == np.float64 else np.int32))
+        sabs = oracle.bin_particles(w.x, w.y, [np.abs(a) for a in w.attrs], w.lo, w.hi, w.res, auto)["sum"]
+        both_nan = np.isnan(got["sum"]) & np.isnan(ref["sum"])
+        assert (both_nan | (np.abs(got["sum"] - ref["sum"]) <= 1e-15 * sabs)).all()
+        assert (np.isnan(got["avg"]) == np.isnan(ref["avg"])).all()
+
+
+def test_threaded_baseline_more_threads_than_particles_and_empty():
+    x = np.array([0.1, 0.9, 0.5]); y = np.array([0.2, 0.8, 0.5]); a = np.array([1.0, 2.0, 3.0])
+    got = oracle.bin_particles_threaded(x, y, [a], res=(2, 2), threads=64)
+    ref = oracle.bin_particles(x, y, [a], res=(2, 2))
+    np.testing.assert_array_equal(got["count"], ref["count"])
+    np.testing.assert_array_equal(got["sum"], ref["sum"])
+    e = np.zeros(0)
+    got = oracle.bin_particles_threaded(e, e, [e], res=(2, 2), threads=4)
+    assert got["count"].sum() == 0 and (got["sum"] == 0).all()
