@@ -24,6 +24,22 @@ template <> __device__ __forceinline__ double vget<double>(const double2& v, int
     return j == 0 ? v.x : v.y;
 }
 
+// Streaming 16-byte column load: evict-first (.cs, the data is read once)
+// with a 256-byte L2 prefetch, so the L2 fetches whole line pairs of the
+// column from DRAM instead of the sectors one warp asked for.
+__device__ __forceinline__ double2 ld_stream(const double2* p) {
+    double2 v;
+    asm("ld.global.cs.L2::256B.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+    float4 v;
+    asm("ld.global.cs.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
 // Mesh location of a particle, -1 when outside.
 template <typename T> struct Binner;
 template <> struct Binner<float> {
@@ -85,6 +101,107 @@ template <> struct KeyOf<double> {
     static constexpr long long kPosInf = 0x7ff0000000000000ll;
     static constexpr long long kNegInf = (long long)(0xfff0000000000000ull ^ 0x7fffffffffffffffull);
 };
+
+// ---------------------------------------------------------------- fixed point
+// Shared-memory sums as integers. GB300's FP64 pipe is narrow and an FP64
+// add to shared memory is a compare-and-swap loop (measured 145 G adds/s
+// over the GPU, against 475 G/s for 64-bit integer adds and 1520 G/s for
+// 32-bit ones). A kernel picks, per attribute, a scale 2^F from the largest
+// exponent among the first values it reads (scale()); a value v whose
+// magnitude lies in the 17 binades below 4x that maximum becomes the
+// integer q = trunc(v * 2^F), |q| < 2^62, losing at most 2^-45 of |v| (f32
+// values convert exactly, over 39 binades); q goes into a 96-bit
+// accumulator: a u64 low word (64-bit integer atomic) and a 32-bit high
+// word that takes the rare carry or borrow (add96). Integer addition is
+// exact and associative, so the accumulated sum is exact up to those
+// conversion losses, in any order. Values outside the range (and NaN,
+// +-inf, subnormals) are not converted: the caller adds them in FP64
+// elsewhere. fixed_value() turns an accumulator back into FP64.
+template <typename T> struct Fixed;
+
+template <> struct Fixed<double> {
+    static constexpr int kExpMax = 0x7ff;  // inf / NaN
+    static constexpr int kDefault = 1023;  // the exponent of 1.0
+    static __device__ __forceinline__ int expo(double v) {
+        return (int)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff;
+    }
+    // The largest sampled biased exponent emax is given two binades of
+    // headroom: |v| < 2^(emax - 1021) maps below 2^62.
+    static __device__ __forceinline__ int scale(int emax) {
+        if (emax <= 0 || emax >= kExpMax) emax = kDefault;
+        return 9 + 1075 - (emax + 2);
+    }
+    // v = +-m * 2^(e - 1075), m the 53-bit significand; q = +-m * 2^sh with
+    // sh = e - 1075 + F. Accepted for -7 <= sh <= 9: |q| < 2^62, and at most
+    // 7 of m's 53 bits are dropped (relative loss < 2^-45). Zero is q = 0.
+    static __device__ __forceinline__ bool to_fixed(double v, int F, long long* q) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        const int e = (int)(b >> 52) & 0x7ff;
+        if (e == 0) {
+            *q = 0;
+            return (b << 1) == 0ull;  // +-0 accepted, subnormals not
+        }
+        const int sh = e - 1075 + F;
+        if (e == kExpMax || sh > 9 || sh < -7) return false;
+        const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+        const unsigned long long mag = sh >= 0 ? (m << sh) : (m >> (-sh));
+        *q = (b >> 63) ? -(long long)mag : (long long)mag;
+        return true;
+    }
+};
+
+template <> struct Fixed<float> {
+    static constexpr int kExpMax = 0xff;
+    static constexpr int kDefault = 127;
+    static __device__ __forceinline__ int expo(float v) { return (int)(__float_as_uint(v) >> 23) & 0xff; }
+    static __device__ __forceinline__ int scale(int emax) {
+        if (emax <= 0 || emax >= kExpMax) emax = kDefault;
+        return 38 + 150 - (emax + 2);
+    }
+    // v = +-m * 2^(e - 150), m the 24-bit significand; exact for
+    // 0 <= sh = e - 150 + F <= 38 (|q| < 2^62).
+    static __device__ __forceinline__ bool to_fixed(float v, int F, long long* q) {
+        const unsigned b = __float_as_uint(v);
+        const int e = (int)(b >> 23) & 0xff;
+        if (e == 0) {
+            *q = 0;
+            return (b << 1) == 0u;
+        }
+        const int sh = e - 150 + F;
+        if (e == kExpMax || sh > 38 || sh < 0) return false;
+        const unsigned long long mag = (unsigned long long)((b & 0x7fffffu) | 0x800000u) << sh;
+        *q = (b >> 31) ? -(long long)mag : (long long)mag;
+        return true;
+    }
+};
+
+// 2^k for -1022 <= k <= 1023, from its bits.
+__device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+
+// The signed 96-bit value hi * 2^64 + lo, times 2^-F, as FP64. The scaling
+// is two multiplications by powers of two (each factor a normal double for
+// |F| <= 2044), exact unless the result falls below the normal range.
+__device__ __forceinline__ double fixed_value(unsigned long long lo, int hi, int F) {
+    double d;
+    if ((hi == 0 && (long long)lo >= 0) || (hi == -1 && (long long)lo < 0))
+        d = __ll2double_rn((long long)lo);  // fits in 64 bits: one rounding
+    else
+        d = __dadd_rn(__dmul_rn((double)hi, 18446744073709551616.0), __ull2double_rn(lo));
+    const int f1 = F / 2;
+    return __dmul_rn(__dmul_rn(d, pow2(-f1)), pow2(f1 - F));
+}
+
+
+// lo/hi += q as one signed 96-bit integer: a carry out of the low word (q
+// >= 0), or an add of a negative q that does not wrap the low word, moves
+// the high word.
+__device__ __forceinline__ void add96(unsigned long long* lo, int* hi, long long q) {
+    const unsigned long long u = (unsigned long long)q;
+    const unsigned long long old = atomicAdd(lo, u);
+    const bool carry = old + u < old;
+    const int d = q >= 0 ? (carry ? 1 : 0) : (carry ? 0 : -1);
+    if (d) atomicAdd(hi, d);
+}
 
 // Shared-memory mesh of B bins. Sums are FP64 for f64 data and for f32 data
 // in kSumF64 mode; FP32 (plus an FP32 compensation term in kSumF32C)
@@ -223,6 +340,56 @@ struct SmemMesh {
                 atomicMax(&kr->y, key);
                 if (h > f.y) atomicMax(&fp->y, h);
             }
+        }
+    }
+
+    // One particle's count and all AC attributes (AC == the mesh's attribute
+    // count). Key modes read every attribute's filter pair first, so the
+    // loads are in flight while the count and the sums update: 16-byte loads
+    // when AC is even (bin b's pairs start at 8 * AC * b bytes, a multiple of
+    // 16 only for even AC), 8-byte loads otherwise.
+    template <int AC>
+    __device__ __forceinline__ void add_particle(int b, const T* v) {
+        if constexpr (kGK && AC > 0) {
+            int2 f[AC];
+            int2* fp = flt + b * AC;
+            if (do_mm) {
+                if constexpr (AC % 2 == 0) {
+#pragma unroll
+                    for (int c = 0; c < AC; c += 2) {
+                        const int4 q = *reinterpret_cast<const int4*>(fp + c);
+                        f[c] = make_int2(q.x, q.y);
+                        f[c + 1] = make_int2(q.z, q.w);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < AC; ++c) f[c] = fp[c];
+                }
+            }
+            add_count(b);
+            if (do_sum)
+#pragma unroll
+                for (int a = 0; a < AC; ++a) atomicAdd(&s64[a * B + b], (double)v[a]);
+            if (!do_mm) return;
+#pragma unroll
+            for (int a = 0; a < AC; ++a) {
+                if (is_nan_bits(v[a])) continue;
+                const K key = KO::key(v[a]);
+                const int h = (int)((long long)key >> 32);  // order preserving
+                K2* kr = gkeys + (int64_t)b * gk_rp + a;
+                if (do_min && h <= f[a].x) {
+                    atomicMin(&kr->x, key);
+                    if (h < f[a].x) atomicMin(&fp[a].x, h);
+                }
+                if (do_max && h >= f[a].y) {
+                    atomicMax(&kr->y, key);
+                    if (h > f[a].y) atomicMax(&fp[a].y, h);
+                }
+            }
+        } else {
+            add_count(b);
+#pragma unroll
+            for (int a = 0; a < AC; ++a) add(a, b, v[a]);
         }
     }
 

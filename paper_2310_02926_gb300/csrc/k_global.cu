@@ -108,12 +108,12 @@ __global__ void __launch_bounds__(NT) k_bin_global(BinArgs args, int64_t head, i
         V x0, y0;
         V av[A_CT > 0 ? A_CT : 1];
         if (live) {
-            x0 = __ldcs(XV + gi);
-            y0 = __ldcs(YV + gi);
+            x0 = ld_stream(XV + gi);
+            y0 = ld_stream(YV + gi);
             if (A_CT > 0) {
 #pragma unroll
                 for (int a = 0; a < A_CT; ++a)
-                    av[a] = __ldcs(reinterpret_cast<const V*>(static_cast<const T*>(args.a[a]) + head) + gi);
+                    av[a] = ld_stream(reinterpret_cast<const V*>(static_cast<const T*>(args.a[a]) + head) + gi);
             }
         }
 #pragma unroll

@@ -81,10 +81,10 @@ __global__ void __launch_bounds__(NT, 1) k_bin_private(BinArgs args, int64_t hea
             for (int u = 0; u < U; ++u) {
                 const int64_t gg = g + u * nthreads;
                 if (gg < groups) {
-                    st.x[u] = __ldcs(XV + gg);
-                    st.y[u] = __ldcs(YV + gg);
+                    st.x[u] = ld_stream(XV + gg);
+                    st.y[u] = ld_stream(YV + gg);
 #pragma unroll
-                    for (int a = 0; a < A_CT; ++a) st.a[u][a] = __ldcs(AV[a] + gg);
+                    for (int a = 0; a < A_CT; ++a) st.a[u][a] = ld_stream(AV[a] + gg);
                 }
             }
         };
@@ -96,9 +96,10 @@ __global__ void __launch_bounds__(NT, 1) k_bin_private(BinArgs args, int64_t hea
                 for (int j = 0; j < VN; ++j) {
                     const int b = binner.bin(vget<T>(st.x[u], j), vget<T>(st.y[u], j));
                     if (b >= 0) {
-                        m.add_count(b);
+                        T v[AC];
 #pragma unroll
-                        for (int a = 0; a < A_CT; ++a) m.add(a, b, vget<T>(st.a[u][a], j));
+                        for (int a = 0; a < A_CT; ++a) v[a] = vget<T>(st.a[u][a], j);
+                        m.template add_particle<A_CT>(b, v);
                     }
                 }
             }
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(NT, 1) k_bin_private(BinArgs args, int64_t hea
         }
     } else {
         for (int64_t gi = tid; gi < groups; gi += nthreads) {
-            V x0 = __ldcs(XV + gi), y0 = __ldcs(YV + gi);
+            V x0 = ld_stream(XV + gi), y0 = ld_stream(YV + gi);
 #pragma unroll
             for (int j = 0; j < VN; ++j) {
                 int b = binner.bin(vget<T>(x0, j), vget<T>(y0, j));

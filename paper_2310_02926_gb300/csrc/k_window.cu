@@ -5,21 +5,12 @@
 // GPU cost, and a centrally concentrated body set piles most particles
 // into few bins).
 //
-// Shared-memory sums are fixed-point integers, not FP64: GB300's FP64 pipe
-// is narrow, and an FP64 add to shared memory is a compare-and-swap loop
-// (measured 145 G adds/s over the GPU, against 475 G/s for 64-bit integer
-// adds and 1520 G/s for 32-bit ones). Each CTA picks, per attribute, a scale
-// 2^F from the largest exponent among the first values it reads. A value v
-// whose magnitude lies in a 17-binade range below that maximum becomes the
-// integer q = trunc(v * 2^F), |q| < 2^62, losing at most 2^-45 of |v|
-// (f32 values are converted exactly); q is added to a 96-bit accumulator
-// (a u64 low word with a 64-bit integer atomic, and a 32-bit high word that
-// takes the rare carry or borrow). Integer addition is exact and
-// associative, so a window sum is exact up to those conversion losses,
-// whatever the order. Values outside the range (and NaN, +-inf,
-// subnormals) go to the FP64 atomic in global memory like every particle
-// outside the window. At the end each CTA converts its window sums to FP64
-// and merges them, with its counts, into the global mesh.
+// Window sums are the 96-bit fixed-point integers of bn_device.cuh (Fixed,
+// add96): exact integer adds in shared memory, no FP64 pipe. Values the
+// CTA's scale cannot hold (and NaN, +-inf, subnormals) go to the FP64
+// atomic in global memory like every particle outside the window. At the
+// end each CTA converts its window sums to FP64 and merges them, with its
+// counts, into the global mesh.
 //
 // Per-bin error of a window sum: at most 2^-45 * sum|a| from the
 // conversions, plus one rounding of the converted partial and the FP64
@@ -34,81 +25,6 @@
 #include "bn_kernels.h"
 
 namespace bn {
-
-// ---------------------------------------------------------------- fixed point
-template <typename T> struct Fixed;
-
-template <> struct Fixed<double> {
-    static constexpr int kExpMax = 0x7ff;  // inf / NaN
-    static constexpr int kDefault = 1023;  // the exponent of 1.0
-    static __device__ __forceinline__ int expo(double v) {
-        return (int)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff;
-    }
-    // The largest sampled biased exponent emax is given two binades of
-    // headroom: |v| < 2^(emax - 1021) maps below 2^62.
-    static __device__ __forceinline__ int scale(int emax) {
-        if (emax <= 0 || emax >= kExpMax) emax = kDefault;
-        return 9 + 1075 - (emax + 2);
-    }
-    // v = +-m * 2^(e - 1075), m the 53-bit significand; q = +-m * 2^sh with
-    // sh = e - 1075 + F. Accepted for -7 <= sh <= 9: |q| < 2^62, and at most
-    // 7 of m's 53 bits are dropped (relative loss < 2^-45). Zero is q = 0.
-    static __device__ __forceinline__ bool to_fixed(double v, int F, long long* q) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-        const int e = (int)(b >> 52) & 0x7ff;
-        if (e == 0) {
-            *q = 0;
-            return (b << 1) == 0ull;  // +-0 accepted, subnormals not
-        }
-        const int sh = e - 1075 + F;
-        if (e == kExpMax || sh > 9 || sh < -7) return false;
-        const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
-        const unsigned long long mag = sh >= 0 ? (m << sh) : (m >> (-sh));
-        *q = (b >> 63) ? -(long long)mag : (long long)mag;
-        return true;
-    }
-};
-
-template <> struct Fixed<float> {
-    static constexpr int kExpMax = 0xff;
-    static constexpr int kDefault = 127;
-    static __device__ __forceinline__ int expo(float v) { return (int)(__float_as_uint(v) >> 23) & 0xff; }
-    static __device__ __forceinline__ int scale(int emax) {
-        if (emax <= 0 || emax >= kExpMax) emax = kDefault;
-        return 38 + 150 - (emax + 2);
-    }
-    // v = +-m * 2^(e - 150), m the 24-bit significand; exact for
-    // 0 <= sh = e - 150 + F <= 38 (|q| < 2^62).
-    static __device__ __forceinline__ bool to_fixed(float v, int F, long long* q) {
-        const unsigned b = __float_as_uint(v);
-        const int e = (int)(b >> 23) & 0xff;
-        if (e == 0) {
-            *q = 0;
-            return (b << 1) == 0u;
-        }
-        const int sh = e - 150 + F;
-        if (e == kExpMax || sh > 38 || sh < 0) return false;
-        const unsigned long long mag = (unsigned long long)((b & 0x7fffffu) | 0x800000u) << sh;
-        *q = (b >> 31) ? -(long long)mag : (long long)mag;
-        return true;
-    }
-};
-
-// 2^k for -1022 <= k <= 1023, from its bits.
-__device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
-
-// The signed 96-bit value hi * 2^64 + lo, times 2^-F, as FP64. The scaling
-// is two multiplications by powers of two (each factor a normal double for
-// |F| <= 2044), exact unless the result falls below the normal range.
-__device__ __forceinline__ double fixed_value(unsigned long long lo, int hi, int F) {
-    double d;
-    if ((hi == 0 && (long long)lo >= 0) || (hi == -1 && (long long)lo < 0))
-        d = __ll2double_rn((long long)lo);  // fits in 64 bits: one rounding
-    else
-        d = __dadd_rn(__dmul_rn((double)hi, 18446744073709551616.0), __ull2double_rn(lo));
-    const int f1 = F / 2;
-    return __dmul_rn(__dmul_rn(d, pow2(-f1)), pow2(f1 - F));
-}
 
 // ---------------------------------------------------------------- window
 size_t window_bytes(int cells, int n_attrs, bool do_sum) {
@@ -228,14 +144,7 @@ __global__ void __launch_bounds__(NT, 1) k_bin_window(BinArgs args, int64_t head
                 for (int a = 0; a < A; ++a) {
                     long long q;
                     if (Fixed<T>::to_fixed(v[a], F[a], &q)) {
-                        if (q == 0) continue;
-                        // 96-bit add: carry out of the low word (q >= 0), or
-                        // no borrow-free wrap (q < 0), moves the high word
-                        const unsigned long long u = (unsigned long long)q;
-                        const unsigned long long old = atomicAdd(&lo[a * W + k], u);
-                        const bool carry = old + u < old;
-                        const int d = q >= 0 ? (carry ? 1 : 0) : (carry ? 0 : -1);
-                        if (d) atomicAdd(&hi[a * W + k], d);
+                        if (q != 0) add96(&lo[a * W + k], &hi[a * W + k], q);
                     } else {
                         atomicAdd(&st.sum[a][b], (double)v[a]);
                     }
@@ -269,15 +178,15 @@ __global__ void __launch_bounds__(NT, 1) k_bin_window(BinArgs args, int64_t head
         const int64_t g2 = gi + nthreads;
         const bool live2 = g2 < groups;
         V xv[2], yv[2], av[2][AC];
-        xv[0] = __ldcs(XV + gi);
-        yv[0] = __ldcs(YV + gi);
+        xv[0] = ld_stream(XV + gi);
+        yv[0] = ld_stream(YV + gi);
 #pragma unroll
-        for (int a = 0; a < A; ++a) av[0][a] = __ldcs(reinterpret_cast<const V*>(AT[a] + head) + gi);
+        for (int a = 0; a < A; ++a) av[0][a] = ld_stream(reinterpret_cast<const V*>(AT[a] + head) + gi);
         if (live2) {
-            xv[1] = __ldcs(XV + g2);
-            yv[1] = __ldcs(YV + g2);
+            xv[1] = ld_stream(XV + g2);
+            yv[1] = ld_stream(YV + g2);
 #pragma unroll
-            for (int a = 0; a < A; ++a) av[1][a] = __ldcs(reinterpret_cast<const V*>(AT[a] + head) + g2);
+            for (int a = 0; a < A; ++a) av[1][a] = ld_stream(reinterpret_cast<const V*>(AT[a] + head) + g2);
         }
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
