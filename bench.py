@@ -678,14 +678,34 @@ def run_single(args, name, n, env, with_e2e=True, with_cpu=True, check=False, st
     with torch.cuda.stream(stream):
         out = bn.alloc_outputs(n_attr, B, tdtype, dev, ops=op_bits)
         res_struct = bn.result_struct(out)
+        exchange = None
+        if world > 1 and op_bits == bn.OP_ALL:
+            # every rank bins its own particles onto the same mesh; each step
+            # ends with the one exchange the path has: the partial meshes
+            # combine (SUM, SUM, MIN, MAX over NCCL), then avg is recomputed
+            exchange = torch.empty(bn.bn_exchange_bytes(B, n_attr), dtype=torch.uint8, device=dev)
+            whole = bn.alloc_outputs(n_attr, B, tdtype, dev)
+            whole_struct = bn.result_struct(whole)
+            code = bn.F64 if dt_label == "f64" else bn.F32
 
         def step():
-            return bn.bn_bin_particles(ctx.handle, cols[0], cols[1], cols[2:], g, ops,
-                                       res_struct, sync=False)
+            # request handles of the step's asynchronous calls, released later
+            rs = [bn.bn_bin_particles(ctx.handle, cols[0], cols[1], cols[2:], g, ops, res_struct,
+                                      sync=False)]
+            if exchange is not None:  # all on the context's stream, in order
+                rs.append(bn.bn_exchange_pack(ctx.handle, res_struct, code, n_attr, B, exchange, sync=False))
+                bn.allreduce_exchange(exchange, B, n_attr)
+                rs.append(bn.bn_exchange_unpack(ctx.handle, exchange, code, n_attr, B, bn.OP_ALL,
+                                                whole_struct, sync=False))
+            return rs
+
+        def release(rs):
+            for r in rs:
+                bn.bn_request_release(r)
 
         clocks = ClockSampler(local).start()
         for _ in range(args.warmup):
-            bn.bn_request_release(step())
+            release(step())
         stream.synchronize()
         bn.bn_context_profile(ctx.handle)  # forget warm-up launches
         launches0 = ctx.launches
@@ -702,8 +722,8 @@ def run_single(args, name, n, env, with_e2e=True, with_cpu=True, check=False, st
         torch.cuda.synchronize(dev)
         if pg:
             pg.barrier()
-        for r in reqs:
-            bn.bn_request_release(r)
+        for rs in reqs:
+            release(rs)
         elapsed_ms = ev0.elapsed_time(ev1)
         gpu_launches = ctx.launches - launches0
         kern_ms, kern_launches, strategy = bn.bn_context_profile(ctx.handle)
@@ -768,7 +788,8 @@ def run_single(args, name, n, env, with_e2e=True, with_cpu=True, check=False, st
         "config": dict(workload_config(name, n, bytes_in), strategy=strategy,
                        autotuner=tuning, ops=args.ops,
                        sum_mode=args.sum if dt_label == "f32" else "f64",
-                       parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+                       parallelism=(f"{world} ranks, each binning its own {n:,} particles; partial meshes combined "
+                     f"every step (exchange buffer, NCCL all-reduce)") if world > 1 else "single GPU"),
         "hbm_frac_step": step_gbs / hbm,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": traffic,

@@ -399,6 +399,53 @@ BN_API bn_status bn_merge_results(bn_context* ctx, const bn_result* parts, int n
                            int32_t dtype, int n_attrs, int64_t bins, uint32_t ops,
                            bn_result* out, int sync, bn_request** req);
 
+/* ----------------------------------------------------------------- ranks */
+
+/*
+ * Partial meshes across ranks. Sec. 4.2 parallelises the binning with MPI:
+ * each rank bins the bodies of its own subdomain onto the same mesh, and
+ * the partial meshes combine. The library packs a rank's result into an
+ * exchange buffer of four sections, each combined across ranks by one
+ * element-wise collective the caller runs (ncclAllReduce, MPI_Allreduce,
+ * torch.distributed.all_reduce):
+ *   bytes [0, 8B)            count  u64 [B]      reduce with SUM
+ *   bytes [8B, 8B(1+A))      sum    f64 [A][B]   reduce with SUM
+ *   bytes [8B(1+A), 8B(1+2A)) minkey s64 [A][B]  reduce with MIN
+ *   bytes [8B(1+2A), 8B(1+3A)) maxkey s64 [A][B] reduce with MAX
+ * (B bins, A attributes; per-attribute arrays attribute-major). A key is the
+ * IEEE totalOrder key of the min or max value as a signed integer (the bits
+ * of a non-negative value; a negative value's bits with the 63 (f64) or 31
+ * (f32) magnitude bits flipped, f32 keys sign-extended to 64 bits), so
+ * integer MIN / MAX are totalOrder min / max: -0 < +0, and the empty-bin
+ * values +inf / -inf are the identities. A float MIN / MAX on the values
+ * themselves would not order -0 and +0.
+ */
+
+/* Bytes of the exchange buffer of a mesh of `bins` bins and n_attrs
+ * attributes (0 for arguments out of range). */
+BN_API size_t bn_exchange_bytes(int64_t bins, int n_attrs);
+
+/* Pack `partial` (count, sum, min and max of every attribute: device
+ * buffers of the context's device, as bn_bin_particles or bn_merge_results
+ * wrote them) into `exchange`, a device buffer of bn_exchange_bytes bytes,
+ * 8-byte aligned. dtype is the min/max type. Request semantics as
+ * bn_bin_particles. */
+BN_API bn_status bn_exchange_pack(bn_context* ctx, const bn_result* partial, int32_t dtype, int n_attrs,
+                                  int64_t bins, void* exchange, int sync, bn_request** req);
+
+/* After the collective: write count and the outputs `ops` selects (sum,
+ * min, max, avg = sum / count, recomputed) from `exchange` into `out`
+ * (device buffers of the context's device). */
+BN_API bn_status bn_exchange_unpack(bn_context* ctx, const void* exchange, int32_t dtype, int n_attrs,
+                                    int64_t bins, uint32_t ops, bn_result* out, int sync, bn_request** req);
+
+/* Automatic device placement (Sec. 3, Eq. 1): the device a rank's in situ
+ * work runs on, d = ((rank mod n_use) * stride + offset) mod n_avail.
+ * n_use <= 0 and stride <= 0 take the paper's defaults (n_use = n_avail,
+ * stride = 1; offset defaults to 0). A negative result of the sum wraps
+ * into [0, n_avail). BN_ERR_INVALID_ARG for rank < 0 or n_avail < 1. */
+BN_API bn_status bn_select_device(int rank, int n_use, int stride, int offset, int n_avail, int* device);
+
 /* ----------------------------------------------------------------- requests */
 
 /* BN_OK when done without error, BN_NOT_READY while running, else the

@@ -248,6 +248,81 @@ def bn_bin_multi(ctx: int, cols: Sequence, specs: Sequence[bn_grid_spec], ops: i
     return None if sync else req.value
 
 
+def bn_exchange_bytes(bins: int, n_attrs: int) -> int:
+    return int(lib().bn_exchange_bytes(bins, n_attrs))
+
+
+def bn_exchange_pack(ctx: int, partial: bn_result, dtype: int, n_attrs: int, bins: int, exchange,
+                     sync: bool = True) -> Optional[int]:
+    """Pack a rank's result into the exchange buffer (a CUDA uint8 tensor of
+    bn_exchange_bytes bytes)."""
+    req = ctypes.c_void_p()
+    check(lib().bn_exchange_pack(ctx, ctypes.byref(partial), dtype, n_attrs, bins, exchange.data_ptr(),
+                                 1 if sync else 0, None if sync else ctypes.byref(req)))
+    return None if sync else req.value
+
+
+def bn_exchange_unpack(ctx: int, exchange, dtype: int, n_attrs: int, bins: int, ops: int, out: bn_result,
+                       sync: bool = True) -> Optional[int]:
+    req = ctypes.c_void_p()
+    check(lib().bn_exchange_unpack(ctx, exchange.data_ptr(), dtype, n_attrs, bins, ops, ctypes.byref(out),
+                                   1 if sync else 0, None if sync else ctypes.byref(req)))
+    return None if sync else req.value
+
+
+def bn_select_device(rank: int, n_avail: int, n_use: int = 0, stride: int = 0, offset: int = 0) -> int:
+    """The paper's automatic placement rule (Eq. 1) for this rank."""
+    d = ctypes.c_int(-1)
+    check(lib().bn_select_device(rank, n_use, stride, offset, n_avail, ctypes.byref(d)))
+    return d.value
+
+
+def exchange_sections(exchange, bins: int, n_attrs: int):
+    """Views of the exchange buffer's four sections (count, sum, minkey,
+    maxkey) as int64 / float64 tensors; counts stay below 2^63."""
+    torch = _torch()
+    B, A = int(bins), int(n_attrs)
+    e = exchange.view(torch.uint8)
+    cut = [0, 8 * B, 8 * B * (1 + A), 8 * B * (1 + 2 * A), 8 * B * (1 + 3 * A)]
+    types = (torch.int64, torch.float64, torch.int64, torch.int64)
+    return [e[cut[k]:cut[k + 1]].view(types[k]) for k in range(4)]
+
+
+def allreduce_exchange(exchange, bins: int, n_attrs: int, group=None) -> None:
+    """Combine the exchange buffers of every rank of `group` in place: counts
+    and sums with SUM, min keys with MIN, max keys with MAX (one collective
+    per section). A gloo group reduces CPU copies of CUDA sections."""
+    import torch.distributed as dist
+    ops = (dist.ReduceOp.SUM, dist.ReduceOp.SUM, dist.ReduceOp.MIN, dist.ReduceOp.MAX)
+    host_only = dist.get_backend(group) == "gloo"
+    for sec, op in zip(exchange_sections(exchange, bins, n_attrs), ops):
+        if sec.numel() == 0:
+            continue
+        if host_only and sec.is_cuda:
+            tmp = sec.cpu()
+            dist.all_reduce(tmp, op=op, group=group)
+            sec.copy_(tmp)
+        else:
+            dist.all_reduce(sec, op=op, group=group)
+
+
+def reduce_across_ranks(ctx: "Context", partial: Dict[str, object], dtype: int, n_attrs: int, bins: int,
+                        ops: int = OP_ALL, group=None,
+                        out: Optional[Dict[str, object]] = None) -> Dict[str, object]:
+    """The whole mesh from every rank's partial result (count, sum, min, max):
+    pack, one collective per section, unpack (avg recomputed)."""
+    torch = _torch()
+    dev = torch.device("cuda", ctx.device)
+    ex = torch.empty(bn_exchange_bytes(bins, n_attrs), dtype=torch.uint8, device=dev)
+    bn_exchange_pack(ctx.handle, result_struct(partial), dtype, n_attrs, bins, ex)
+    allreduce_exchange(ex, bins, n_attrs, group)
+    if out is None:
+        tdt = torch.float64 if dtype == F64 else torch.float32
+        out = alloc_outputs(n_attrs, bins, tdt, dev, ops | OP_COUNT)
+    bn_exchange_unpack(ctx.handle, ex, dtype, n_attrs, bins, ops, result_struct(out))
+    return out
+
+
 def bn_query(req: int) -> int:
     return check(lib().bn_query(req))
 

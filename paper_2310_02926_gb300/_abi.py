@@ -154,6 +154,13 @@ PROTOTYPES = {
     "bn_server_submit": (S, [P, ctypes.POINTER(bn_block), ctypes.c_uint32, PP]),
     "bn_server_stats_get": (S, [P, ctypes.POINTER(bn_server_stats)]),
     "bn_server_request_timing": (S, [P, ctypes.POINTER(bn_request_timing)]),
+    "bn_exchange_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int]),
+    "bn_exchange_pack": (S, [P, ctypes.POINTER(bn_result), ctypes.c_int32, ctypes.c_int, ctypes.c_int64,
+                             P, ctypes.c_int, PP]),
+    "bn_exchange_unpack": (S, [P, P, ctypes.c_int32, ctypes.c_int, ctypes.c_int64, ctypes.c_uint32,
+                               ctypes.POINTER(bn_result), ctypes.c_int, PP]),
+    "bn_select_device": (S, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_int)]),
     "bn_server_destroy": (S, [P]),
     "bn_nbody_step": (S, [P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.c_int64, ctypes.c_float,
                           ctypes.c_float, P]),

@@ -74,7 +74,19 @@ namespace bn {
 bn_status fail(bn_status st, const char* fmt, ...);
 bn_status cuda_fail(cudaError_t e, const char* what);
 
-struct DeviceGuard;
+// Makes `dev` the calling thread's current device for its scope.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
 
 // Everything one request queues: stream ordering, staged inputs,
 // temporaries (freed stream-ordered once the kernels are queued) and

@@ -50,22 +50,6 @@ extern "C" const char* bn_version(void) { return "binning 0.1 (sm_103a)"; }
     } while (0)
 
 // ------------------------------------------------------------------ context
-namespace bn {
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-}  // namespace bn
 
 static const int kStatusSlots = 4096;
 
