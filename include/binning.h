@@ -30,8 +30,16 @@
  *    column in page-locked (pinned or registered) host memory is read in
  *    place by the kernels over the host link; other host inputs, and host
  *    outputs, go through a device temporary.
- *  - A buffer on a different CUDA device than the context's is rejected
- *    with BN_ERR_DEVICE_MISMATCH.
+ *  - A buffer on a different CUDA device of this process is reached the
+ *    same way (location-agnostic access, Sec. 2: GetCUDAAccessible moves
+ *    another device's data to the one doing the work): an input column is
+ *    copied peer to peer into a temporary of the context's device after the
+ *    work queued on its owning stream (on its own device); an output is
+ *    written to a temporary and copied to its device when the request
+ *    completes, and later work on its owning stream waits for that copy.
+ *    The server (bn_server_submit) takes host buffers and buffers of the
+ *    context's device only. A device ordinal this process does not have is
+ *    rejected with BN_ERR_DEVICE_MISMATCH.
  *
  * Bin layout of every per-bin output: row-major [res_y][res_x], bin
  * b = iy * res_x + ix. Per-attribute outputs are separate buffers.
@@ -81,7 +89,7 @@ typedef enum bn_status {
     BN_OK = 0,
     BN_NOT_READY = 1,            /* bn_query: the request is still running */
     BN_ERR_INVALID_ARG = -1,     /* bad dtype, length mismatch, res out of range, lo >= hi, ... */
-    BN_ERR_DEVICE_MISMATCH = -2, /* a buffer lives on another CUDA device */
+    BN_ERR_DEVICE_MISMATCH = -2, /* a buffer's device cannot be used for this call */
     BN_ERR_NO_MEMORY = -3,       /* a device or host allocation failed */
     BN_ERR_BUDGET = -4,          /* a server request can never fit the memory budget */
     BN_ERR_TIMEOUT = -5,         /* bn_wait gave up; the request is still running */

@@ -25,7 +25,7 @@ struct KernelCtx {
 cudaError_t launch_init_state(const KernelCtx& kc, int dtype, const StateDesc& st,
                               void* bounds_acc);
 cudaError_t launch_bounds_reduce(const KernelCtx& kc, int dtype, const void* x, const void* y,
-                                 int64_t n, void* bounds_acc);
+                                 int64_t n, void* bounds_acc, int64_t sx = 1, int64_t sy = 1);
 cudaError_t launch_grid_setup(const KernelCtx& kc, int dtype, const GridDesc& host_desc,
                               const void* bounds_acc, GridDesc* dev_desc, long long* edges0,
                               long long* edges1, double* bounds_out, int* status);
@@ -49,6 +49,11 @@ struct BinArgs {
     const void* x;
     const void* y;
     const void* a[kMaxAttr];
+    // element strides of x, y and the attributes (0 or 1: contiguous). The
+    // private, global and window kernels read strided columns in place with
+    // scalar loads (a warp's loads of consecutive records cover contiguous
+    // memory); the other kernels take contiguous columns only.
+    int64_t sx, sy, sa[kMaxAttr];
     int64_t n;
     GridDesc grid;          // by value (explicit bounds) ...
     const GridDesc* dev_grid;  // ... or read on the device (automatic bounds; null otherwise)

@@ -103,8 +103,16 @@ struct Plan {
     std::vector<void*> waited;
     std::vector<void*> out_streams;
     std::vector<Copy> d2h;
+    struct PeerCopy {  // an output on another device: temporary -> peer at finish
+        void* peer;
+        int device;
+        void* stream;
+        void* dev;
+        size_t bytes;
+    };
+    std::vector<PeerCopy> peer_out;
     cudaError_t err = cudaSuccess;
-    size_t h2d_bytes = 0, d2h_bytes = 0;
+    size_t h2d_bytes = 0, d2h_bytes = 0, p2p_bytes = 0;
     size_t temp_bytes = 0;  // bytes of every temporary alloc() handed out
     int strategy = 0;
     // false: an unseen shape class takes the heuristic strategy instead of
@@ -118,7 +126,8 @@ struct Plan {
     void* alloc(size_t bytes);
     void free_temps();
     bn_status wait_on(void* stream);
-    bn_status column(const bn_buffer* b, int dtype, const void** out);
+    bn_status wait_on_peer(void* stream, int device);
+    bn_status column(const bn_buffer* b, int dtype, const void** out, int64_t* stride_out = nullptr);
     bn_status output(bn_buffer* b, bool wanted, int64_t bins, int dtype, bool load, void** out);
     bn_status finish(bn_request* r);
 };

@@ -101,14 +101,14 @@ template <> __device__ __forceinline__ bool finite_bits<double>(double v) {
 // {min x, max x, min y, max y}.
 template <typename T>
 __global__ void k_bounds_reduce(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
-                                T* bounds_acc) {
+                                T* bounds_acc, int64_t sx, int64_t sy) {
     using K = typename KeyT<T>::type;
     const K kmax = (K)(~(typename std::make_unsigned<K>::type)0 >> 1);
     const K kmin = -kmax - 1;
     K mnx = kmax, mxx = kmin, mny = kmax, mxy = kmin;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        T vx = x[i], vy = y[i];
+        T vx = x[i * sx], vy = y[i * sy];
         if (finite_bits(vx)) {
             K k = ordered_key(vx);
             mnx = min(mnx, k);
@@ -321,17 +321,19 @@ cudaError_t launch_init_state(const KernelCtx& kc, int dtype, const StateDesc& s
 }
 
 cudaError_t launch_bounds_reduce(const KernelCtx& kc, int dtype, const void* x, const void* y,
-                                 int64_t n, void* bounds_acc) {
+                                 int64_t n, void* bounds_acc, int64_t sx, int64_t sy) {
     const int block = 256;
     int grid = grid_for(n, block, kc.num_sms * 8);
+    sx = sx > 1 ? sx : 1;
+    sy = sy > 1 ? sy : 1;
     if (dtype == BN_F64)
         k_bounds_reduce<double><<<grid, block, 0, kc.stream>>>(
             static_cast<const double*>(x), static_cast<const double*>(y), n,
-            static_cast<double*>(bounds_acc));
+            static_cast<double*>(bounds_acc), sx, sy);
     else
         k_bounds_reduce<float><<<grid, block, 0, kc.stream>>>(
             static_cast<const float*>(x), static_cast<const float*>(y), n,
-            static_cast<float*>(bounds_acc));
+            static_cast<float*>(bounds_acc), sx, sy);
     kc.count_launch();
     return cudaGetLastError();
 }

@@ -85,14 +85,17 @@ __global__ void __launch_bounds__(NT) k_bin_global(BinArgs args, int64_t head, i
     // every lane), lanes past the end pass b = -1
     const int64_t tail0 = head + groups * VN;
     const int64_t warp_base = tid - (threadIdx.x & 31);
+    // scalar path: strided columns are read in place
+    const int64_t sx = args.sx > 1 ? args.sx : 1, sy = args.sy > 1 ? args.sy : 1;
     auto scalar_range = [&](int64_t r0, int64_t r1) {
         for (int64_t base = r0 + warp_base; base < r1; base += nthreads) {
             const int64_t i = base + (threadIdx.x & 31);
             T v[AC];
             int b = -1;
             if (i < r1) {
-                b = binner.bin(X[i], Y[i]);
-                for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(args.a[a])[i];
+                b = binner.bin(X[i * sx], Y[i * sy]);
+                for (int a = 0; a < A; ++a)
+                    v[a] = static_cast<const T*>(args.a[a])[i * (args.sa[a] > 1 ? args.sa[a] : 1)];
             }
             warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0);
         }
@@ -143,7 +146,9 @@ static void gvector_split(const BinArgs& a, int64_t* head, int64_t* groups) {
     int ph = phase(a.x);
     bool same = aligned && phase(a.y) == ph;
     for (int k = 0; k < a.n_attrs; ++k) same = same && phase(a.a[k]) == ph;
-    if (!same) {
+    bool strided = a.sx > 1 || a.sy > 1;
+    for (int k = 0; k < a.n_attrs; ++k) strided = strided || a.sa[k] > 1;
+    if (!same || strided) {
         *head = a.n;
         *groups = 0;
         return;

@@ -49,11 +49,16 @@ __global__ void __launch_bounds__(NT, 1) k_bin_private(BinArgs args, int64_t hea
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 
+    // scalar path: strided columns are read in place
+    const int64_t sx = args.sx > 1 ? args.sx : 1, sy = args.sy > 1 ? args.sy : 1;
     auto one = [&](int64_t i) {
-        int b = binner.bin(X[i], Y[i]);
+        int b = binner.bin(X[i * sx], Y[i * sy]);
         if (b < 0) return;
         m.add_count(b);
-        for (int a = 0; a < A; ++a) m.add(a, b, static_cast<const T*>(args.a[a])[i]);
+        for (int a = 0; a < A; ++a) {
+            const int64_t sa = args.sa[a] > 1 ? args.sa[a] : 1;
+            m.add(a, b, static_cast<const T*>(args.a[a])[i * sa]);
+        }
     };
 
     // scalar head (until every column is 16-byte aligned) and tail
@@ -139,7 +144,9 @@ static void vector_split(const BinArgs& a, int64_t* head, int64_t* groups) {
     int ph = phase(a.x);
     bool same = aligned && phase(a.y) == ph;
     for (int k = 0; k < a.n_attrs; ++k) same = same && phase(a.a[k]) == ph;
-    if (!same) {
+    bool strided = a.sx > 1 || a.sy > 1;
+    for (int k = 0; k < a.n_attrs; ++k) strided = strided || a.sa[k] > 1;
+    if (!same || strided) {
         *head = a.n;
         *groups = 0;
         return;

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(NT, 1) k_bin_window(BinArgs args, int64_t head
                 }
         } else if (tid < n) {
 #pragma unroll
-            for (int a = 0; a < AC; ++a) see(a, AT[a][tid]);
+            for (int a = 0; a < AC; ++a) see(a, AT[a][tid * (args.sa[a] > 1 ? args.sa[a] : 1)]);
         }
 #pragma unroll
         for (int a = 0; a < AC; ++a) {
@@ -159,19 +159,19 @@ __global__ void __launch_bounds__(NT, 1) k_bin_window(BinArgs args, int64_t head
         if (A > 0) commit_minmax<T, A>(st, A, b, v, v);
     };
 
-    // scalar head and tail
-    for (int64_t i = tid; i < head; i += nthreads) {
+    // scalar head and tail; strided columns are read in place here
+    const int64_t sx = args.sx > 1 ? args.sx : 1, sy = args.sy > 1 ? args.sy : 1;
+    int64_t sa[AC];
+#pragma unroll
+    for (int a = 0; a < AC; ++a) sa[a] = args.sa[a] > 1 ? args.sa[a] : 1;
+    auto scalar = [&](int64_t i) {
         T v[AC];
 #pragma unroll
-        for (int a = 0; a < A; ++a) v[a] = AT[a][i];
-        one(X[i], Y[i], v);
-    }
-    for (int64_t i = head + groups * VN + tid; i < n; i += nthreads) {
-        T v[AC];
-#pragma unroll
-        for (int a = 0; a < A; ++a) v[a] = AT[a][i];
-        one(X[i], Y[i], v);
-    }
+        for (int a = 0; a < A; ++a) v[a] = AT[a][i * sa[a]];
+        one(X[i * sx], Y[i * sy], v);
+    };
+    for (int64_t i = tid; i < head; i += nthreads) scalar(i);
+    for (int64_t i = head + groups * VN + tid; i < n; i += nthreads) scalar(i);
     // vector groups, two per thread and iteration so that more loads are in
     // flight while the atomics of the previous ones drain
     for (int64_t gi = tid; gi < groups; gi += 2 * nthreads) {
@@ -226,7 +226,9 @@ static void window_split(const BinArgs& a, int64_t* head, int64_t* groups) {
     const int ph = phase(a.x);
     bool same = phase(a.y) == ph;
     for (int k = 0; k < a.n_attrs; ++k) same = same && phase(a.a[k]) == ph;
-    if (!same) {
+    bool strided = a.sx > 1 || a.sy > 1;
+    for (int k = 0; k < a.n_attrs; ++k) strided = strided || a.sa[k] > 1;
+    if (!same || strided) {
         *head = a.n;
         *groups = 0;
         return;

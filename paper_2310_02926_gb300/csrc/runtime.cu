@@ -308,9 +308,15 @@ bn_status bn::validate_buffer(const bn_context* c, const bn_buffer* b, int64_t n
         return fail(BN_ERR_INVALID_ARG, "%s: dtype %d, expected %d", what, b->dtype, dtype);
     if (n > 0 && !b->ptr) return fail(BN_ERR_INVALID_ARG, "%s: NULL pointer", what);
     if (b->stride < 0) return fail(BN_ERR_INVALID_ARG, "%s: negative stride", what);
-    if (b->device != BN_HOST && b->device != c->device)
-        return fail(BN_ERR_DEVICE_MISMATCH, "%s: buffer on device %d, context on device %d", what,
-                    b->device, c->device);
+    if (b->device != BN_HOST && b->device != c->device) {
+        // another CUDA device of this process: staged (Plan::column)
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || b->device < 0 || b->device >= ndev) {
+            cudaGetLastError();
+            return fail(BN_ERR_DEVICE_MISMATCH, "%s: buffer on device %d, which this process does not have", what,
+                        b->device);
+        }
+    }
     if (b->ptr && ((uintptr_t)b->ptr % (uintptr_t)dtype_size(dtype)) != 0)
         return fail(BN_ERR_INVALID_ARG, "%s: pointer not aligned to its element size", what);
     return BN_OK;
@@ -382,6 +388,22 @@ void Plan::free_temps() {
     temps.clear();
 }
 
+// Order the execution stream after work already queued on stream s of
+// another device: the event is created and recorded on that device.
+bn_status Plan::wait_on_peer(void* s, int device) {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e;
+    {
+        DeviceGuard g(device);
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, static_cast<cudaStream_t>(s));
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev, 0);
+    if (ev) cudaEventDestroy(ev);  // released once the wait has been satisfied
+    if (e != cudaSuccess) return cuda_fail(e, "stream ordering (peer device)");
+    return BN_OK;
+}
+
 // Order the execution stream after work already queued on stream s.
 bn_status Plan::wait_on(void* s) {
     cudaStream_t st = static_cast<cudaStream_t>(s);
@@ -398,9 +420,12 @@ bn_status Plan::wait_on(void* s) {
     return BN_OK;
 }
 
-// A device pointer with the column's data, contiguous: the buffer itself
-// (zero copy), or a staged copy (host data, or strided device data).
-bn_status Plan::column(const bn_buffer* b, int dtype, const void** out) {
+// A device pointer with the column's data: the buffer itself (zero copy), or
+// a contiguous staged copy (host data, or strided device data when the
+// caller cannot read strided columns: stride_out == nullptr). With
+// stride_out, a strided device column is used in place and its element
+// stride returned (1 otherwise).
+bn_status Plan::column(const bn_buffer* b, int dtype, const void** out, int64_t* stride_out) {
     const size_t es = dtype_size(dtype);
     const int64_t n = b->n;
     if (n == 0) {
@@ -408,11 +433,42 @@ bn_status Plan::column(const bn_buffer* b, int dtype, const void** out) {
         return BN_OK;
     }
     const int64_t stride = b->stride <= 1 ? 1 : b->stride;
+    if (stride_out) *stride_out = 1;
+    if (b->device != BN_HOST && b->device != ctx->device) {
+        // another device (location-agnostic access, Sec. 2: moved to the
+        // device that runs the work, into a temporary freed with the
+        // request): one peer copy of the column's span, after the work
+        // queued on its owning stream
+        bn_status st = wait_on_peer(b->stream, b->device);
+        if (st != BN_OK) return st;
+        const size_t span = ((size_t)(n - 1) * stride + 1) * es;
+        void* t = alloc(span);
+        if (!t) return cuda_fail(err, "cudaMallocAsync(peer column)");
+        cudaError_t e = cudaMemcpyPeerAsync(t, ctx->device, b->ptr, b->device, span, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy column from peer device");
+        p2p_bytes += span;
+        if (stride == 1 || stride_out) {
+            if (stride_out) *stride_out = stride;
+            *out = t;
+            return BN_OK;
+        }
+        void* g = alloc((size_t)n * es);
+        if (!g) return cuda_fail(err, "cudaMallocAsync(column)");
+        e = launch_gather(kc(), dtype, g, t, n, stride);
+        if (e != cudaSuccess) return cuda_fail(e, "gather kernel");
+        *out = g;
+        return BN_OK;
+    }
     if (b->device != BN_HOST) {
         bn_status st = wait_on(b->stream);
         if (st != BN_OK) return st;
         if (stride == 1) {
             *out = b->ptr;
+            return BN_OK;
+        }
+        if (stride_out) {
+            *out = b->ptr;
+            *stride_out = stride;
             return BN_OK;
         }
         void* t = alloc((size_t)n * es);
@@ -462,9 +518,29 @@ bn_status Plan::output(bn_buffer* b, bool wanted, int64_t bins, int dtype, bool 
                                      (long long)b->n, (long long)bins);
         if (b->dtype != dtype) return fail(BN_ERR_INVALID_ARG, "output dtype %d, expected %d", b->dtype, dtype);
         if (b->stride > 1) return fail(BN_ERR_INVALID_ARG, "output buffers must be contiguous");
-        if (b->device != BN_HOST && b->device != ctx->device)
-            return fail(BN_ERR_DEVICE_MISMATCH, "output on device %d, context on device %d", b->device, ctx->device);
         if (((uintptr_t)b->ptr % es) != 0) return fail(BN_ERR_INVALID_ARG, "output pointer misaligned");
+        if (b->device != BN_HOST && b->device != ctx->device) {
+            // another device: a temporary here, copied to the peer buffer when
+            // the work is done, ordered before later work on its stream
+            int ndev = 0;
+            if (cudaGetDeviceCount(&ndev) != cudaSuccess || b->device < 0 || b->device >= ndev) {
+                cudaGetLastError();
+                return fail(BN_ERR_DEVICE_MISMATCH, "output on device %d, which this process does not have",
+                            b->device);
+            }
+            bn_status st = wait_on_peer(b->stream, b->device);
+            if (st != BN_OK) return st;
+            void* t = alloc((size_t)bins * es);
+            if (!t) return cuda_fail(err, "cudaMallocAsync(peer output)");
+            if (load) {
+                cudaError_t e = cudaMemcpyPeerAsync(t, ctx->device, b->ptr, b->device, (size_t)bins * es, stream);
+                if (e != cudaSuccess) return cuda_fail(e, "copy peer output in");
+                p2p_bytes += (size_t)bins * es;
+            }
+            peer_out.push_back({b->ptr, b->device, b->stream, t, (size_t)bins * es});
+            *out = t;
+            return BN_OK;
+        }
         if (b->device != BN_HOST) {
             bn_status st = wait_on(b->stream);
             if (st != BN_OK) return st;
@@ -513,9 +589,20 @@ bn_status Plan::finish(bn_request* r) {
         if (e != cudaSuccess) return cuda_fail(e, "copy output to host");
         d2h_bytes += c.bytes;
     }
+    for (auto& c : peer_out) {
+        cudaError_t e = cudaMemcpyPeerAsync(c.peer, c.device, c.dev, ctx->device, c.bytes, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy output to peer device");
+        p2p_bytes += c.bytes;
+    }
     free_temps();
     cudaError_t e = cudaEventRecord(r->done, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    // later work on a peer output's own stream (on its device) waits for it
+    for (auto& c : peer_out) {
+        DeviceGuard g(c.device);
+        e = cudaStreamWaitEvent(static_cast<cudaStream_t>(c.stream), r->done, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "order peer output stream");
+    }
     for (void* s : out_streams) {
         if (static_cast<cudaStream_t>(s) == stream) continue;
         e = cudaStreamWaitEvent(static_cast<cudaStream_t>(s), r->done, 0);
@@ -665,10 +752,16 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
     const uint32_t agg = ops & BN_AGG_MASK;
     args.aggregate = agg == BN_AGG_ON ? 1 : agg == BN_AGG_OFF ? 0
                      : ((int64_t)grid->res[0] * grid->res[1] <= 65536 ? 1 : 0);
-    st = plan.column(x, dtype, &args.x);
-    if (st == BN_OK) st = plan.column(y, dtype, &args.y);
-    for (int a = 0; a < n_attrs && st == BN_OK; ++a) st = plan.column(&attrs[a], dtype, &args.a[a]);
+    // strided device columns are read in place by the private, global and
+    // hybrid kernels; the sort path needs them contiguous
+    const bool sort_forced = (ops & BN_STRATEGY_MASK) == BN_STRATEGY_SORT;
+    st = plan.column(x, dtype, &args.x, sort_forced ? nullptr : &args.sx);
+    if (st == BN_OK) st = plan.column(y, dtype, &args.y, sort_forced ? nullptr : &args.sy);
+    for (int a = 0; a < n_attrs && st == BN_OK; ++a)
+        st = plan.column(&attrs[a], dtype, &args.a[a], sort_forced ? nullptr : &args.sa[a]);
     if (st != BN_OK) return st;
+    bool strided = args.sx > 1 || args.sy > 1;
+    for (int a = 0; a < n_attrs; ++a) strided = strided || args.sa[a] > 1;
 
     StateDesc& sd = args.st;
     sd.bins = B;
@@ -755,6 +848,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
                 trial = true;
             }
         }
+        if (strided && strat == BN_STRATEGY_SORT) strat = BN_STRATEGY_GLOBAL;  // (tuned on contiguous data)
         // a forced window without a tuned placement sits at the mesh centre
         if (strat == BN_STRATEGY_HYBRID && args.win_nx == 0) {
             int wnx = 0, wny = 0;
@@ -786,7 +880,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         sortd.accumulate = accumulate ? 1 : 0;
         if (strat == BN_STRATEGY_SORT && !sort_ok)
             return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_SORT: the mesh has too many buckets for the sort path");
-        if (strat == BN_STRATEGY_SORT || (trial && sort_ok)) {
+        if (strat == BN_STRATEGY_SORT || (trial && sort_ok && !strided)) {
             sort_scratch = plan.alloc(sort_scratch_bytes(sortd, args));
             if (!sort_scratch) return cuda_fail(plan.err, "cudaMallocAsync(sort scratch)");
         }
@@ -814,7 +908,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         }
         if (!dev_grid || (dtype == BN_F64 && (!e0 || !e1))) return cuda_fail(plan.err, "cudaMallocAsync(grid)");
         if (grid->auto_bounds && n > 0) {
-            e = launch_bounds_reduce(kc, dtype, args.x, args.y, n, bounds_acc);
+            e = launch_bounds_reduce(kc, dtype, args.x, args.y, n, bounds_acc, args.sx, args.sy);
             if (e != cudaSuccess) return cuda_fail(e, "bounds kernel");
         }
         e = launch_grid_setup(kc, dtype, gd, bounds_acc, dev_grid, e0, e1, bounds_out, status_dev);

@@ -357,6 +357,16 @@ extern "C" bn_status bn_server_submit(bn_server* s, const bn_block* b, uint32_t 
     if (st == BN_OK) st = validate_buffer(c, &b->y, n, dtype, "y");
     for (int a = 0; a < b->n_attrs && st == BN_OK; ++a) st = validate_buffer(c, &b->attrs[a], n, dtype, "attr");
     if (st != BN_OK) return st;
+    // the deep copy orders itself after the columns' own streams on this
+    // device: columns and outputs on other devices go through bn_bin_particles
+    auto peer = [&](const bn_buffer& q) { return q.ptr && q.device != BN_HOST && q.device != c->device; };
+    bool any_peer = peer(b->x) || peer(b->y) || (b->out && peer(b->out->count));
+    for (int a = 0; a < b->n_attrs; ++a)
+        any_peer = any_peer || peer(b->attrs[a]) ||
+                   (b->out && (peer(b->out->sum[a]) || peer(b->out->min[a]) || peer(b->out->max[a]) ||
+                               peer(b->out->avg[a])));
+    if (any_peer)
+        return fail(BN_ERR_DEVICE_MISMATCH, "bn_server_submit: buffers on another device are not served");
     GridDesc gd;
     st = make_grid_desc(&b->grid, dtype, &gd);
     if (st != BN_OK) return st;

@@ -266,14 +266,24 @@ def test_misaligned_columns(bn, ctx, dtype, strategy, offsets):
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-def test_strided_columns(bn, ctx, dtype):
-    """Array-of-structs columns (element stride 4) are gathered, then binned."""
-    w = workloads.uniform(40_000, seed=6, dtype=dtype, res=24)
-    aos = np.stack([w.x, w.y, *w.attrs], axis=1)
+@pytest.mark.parametrize("strategy", ["auto", "private", "global", "hybrid", "sort"])
+@pytest.mark.parametrize("auto_bounds", [False, True])
+def test_strided_columns(bn, ctx, dtype, strategy, auto_bounds):
+    """Array-of-structs columns (a record of 7 values, the columns at
+    different offsets in it) read in place by the particle pass (private,
+    global, hybrid), or gathered first (sort); with explicit and automatic
+    bounds, and a length that leaves ragged tails."""
+    w = workloads.plummer(150_001, seed=6, dtype=dtype, res=40 if strategy == "private" else 300)
+    rng = np.random.default_rng(7)
+    aos = np.stack([rng.random(w.n).astype(dtype), w.y, w.attrs[2], w.x, w.attrs[0],
+                    rng.random(w.n).astype(dtype), w.attrs[1]], axis=1)
     t = torch.from_numpy(aos).to("cuda")
-    out = ctx.bin_particles(t[:, 0], t[:, 1], [t[:, 2], t[:, 3]], w.lo, w.hi, w.res)
+    flags = sflag(bn, strategy)
+    out = ctx.bin_particles(t[:, 3], t[:, 1], [t[:, 4], t[:, 6], t[:, 2]], w.lo, w.hi, w.res,
+                            auto_bounds, bn.OP_ALL | flags)
     torch.cuda.synchronize()
-    check(w, to_numpy_result(out), TOL_F64 if dtype == np.float64 else TOL_F32C)
+    check(w, to_numpy_result(out), TOL_F64 if dtype == np.float64 else TOL_F32C, auto_bounds=auto_bounds,
+          label=strategy)
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
@@ -588,13 +598,33 @@ def test_invalid_arguments_are_reported(bn, ctx):
                                    1, None)
     assert st == bn.ERR_INVALID_ARG
     bx = bn.buffer(x)
-    bx.device = 7
+    bx.device = torch.cuda.device_count()  # a device this process does not have
     by = bn.buffer(y)
     r = bn.bn_result()
     st = bn.lib().bn_bin_particles(ctx.handle, ctypes.byref(bx), ctypes.byref(by), None, 0,
                                    ctypes.byref(bn.grid()), bn.OP_COUNT, ctypes.byref(r), 1, None)
     assert st == bn.ERR_DEVICE_MISMATCH
     assert b"device" in bn.lib().bn_last_error()
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2,
+                    reason="needs two GPUs (one per box here)")
+@pytest.mark.parametrize("where", ["inputs", "outputs", "both"])
+def test_columns_and_outputs_on_another_device(bn, where):
+    """Location-agnostic access across devices: a context on device 0 bins
+    columns that live on device 1 (copied peer to peer, strided ones
+    included) and/or writes outputs that live on device 1."""
+    w = workloads.plummer(200_001, seed=12, dtype=np.float64, res=128)
+    d_in = torch.device("cuda", 1 if where in ("inputs", "both") else 0)
+    d_out = torch.device("cuda", 1 if where in ("outputs", "both") else 0)
+    aos = torch.from_numpy(np.stack([w.x, w.y, *w.attrs], axis=1)).to(d_in)
+    cols = [aos[:, 0].contiguous(), aos[:, 1], aos[:, 2].contiguous(), aos[:, 3], aos[:, 4]]
+    out = bn.alloc_outputs(3, 128 * 128, torch.float64, d_out)
+    with bn.Context(0) as c:
+        c.bin_particles(cols[0], cols[1], cols[2:], w.lo, w.hi, w.res, out=out)
+        torch.cuda.synchronize(0)
+        torch.cuda.synchronize(1)
+    check(w, to_numpy_result(out), TOL_F64, label=where)
 
 
 # ------------------------------------------------------------------ serving
@@ -804,6 +834,59 @@ def test_gaussians_f32_full_size(bn, ctx):
     """2^27 f32 particles from 16 Gaussians on a 4096x4096 mesh (compensated sums)."""
     w = workloads.gaussians(2 ** 27, seed=0, res=4096)
     check(w, run_gpu(ctx, w), TOL_F32C, label="gaussians full")
+
+
+@pytest.mark.slow
+def test_batch256_full_plan(bn, ctx):
+    """The batching workload at full size: 256 blocks of log-uniform 1e3..1e7
+    f32 particles, each with its own mesh (32^2..2048^2), in one
+    bn_bin_batch call with the autotuned strategy per block (sort blocks
+    included); every block against the oracle."""
+    plan = workloads.batch(n_blocks=256, seed=0)
+    blocks, outs, keep = [], [], []
+    for k in range(plan.n_blocks):
+        w = plan.block(k)
+        cols = [torch.from_numpy(c).cuda() for c in (w.x, w.y, *w.attrs)]
+        o = bn.alloc_outputs(2, w.res[0] * w.res[1], torch.float32, torch.device("cuda"))
+        r = bn.result_struct(o)
+        keep += [cols, r]
+        outs.append(o)
+        blocks.append(bn.block(cols[0], cols[1], cols[2:], bn.grid(w.lo, w.hi, w.res), r))
+    for rep in range(2):  # the second call replays the cached graph
+        for o in outs:
+            for t in [o["count"], *o["sum"]]:
+                t.fill_(3)
+        bn.bn_bin_batch(ctx.handle, blocks, bn.OP_ALL)
+        torch.cuda.synchronize()
+    del keep
+    for k in range(plan.n_blocks):
+        w = plan.block(k)
+        check(w, to_numpy_result(outs[k]), TOL_F32C, label=f"block {k} n={w.n} res={w.res}")
+        outs[k] = None
+
+
+@pytest.mark.slow
+def test_multi_grid_phase_space_full(bn, ctx):
+    """The fused multi-grid workload at full size: 2^22 f64 particles of a
+    Plummer snapshot, 10 variables binned in 9 coordinate systems on 256^2
+    meshes (the paper's 90 binnings per step), every spec against the oracle."""
+    n, res = 2 ** 22, (256, 256)
+    cols = workloads.phase_space(n, seed=0)
+    names = list(cols)
+    tcols = [torch.from_numpy(cols[k]).cuda() for k in names]
+    variables = [names.index(v) for v in workloads.PHASE_SPACE_VARIABLES]
+    specs, keep = [], []
+    for (a, b) in workloads.PHASE_SPACE_SYSTEMS:
+        ha, hb = workloads.PHASE_SPACE_BOUNDS[a], workloads.PHASE_SPACE_BOUNDS[b]
+        specs.append(bn.grid_spec(names.index(a), names.index(b), variables, bn.grid((-ha, -hb), (ha, hb), res)))
+        keep.append(bn.alloc_outputs(len(variables), res[0] * res[1], torch.float64, torch.device("cuda")))
+    bn.bn_bin_multi(ctx.handle, tcols, specs, bn.OP_ALL, [bn.result_struct(o) for o in keep])
+    torch.cuda.synchronize()
+    for k, (a, b) in enumerate(workloads.PHASE_SPACE_SYSTEMS):
+        ha, hb = workloads.PHASE_SPACE_BOUNDS[a], workloads.PHASE_SPACE_BOUNDS[b]
+        w = workloads.Workload(f"{a}-{b}", cols[a], cols[b], [cols[v] for v in workloads.PHASE_SPACE_VARIABLES],
+                               (-ha, -hb), (ha, hb), res)
+        check(w, to_numpy_result(keep[k]), TOL_F64, label=f"system {a}-{b}")
 
 
 # ------------------------------------------------------------------ fused multi-grid pass
