@@ -19,21 +19,71 @@ namespace bn {
 
 // One spec over one tile. K: the spec's attribute count, so that the
 // per-particle values and the commit's partial sums live in registers (-1:
-// any count, through local memory).
+// any count, through local memory). For up to four attributes, when every
+// column of the spec is 16-byte aligned, a lane reads VN consecutive
+// particles with one vector load per column (read-only cache: the next
+// specs of the tile read the same columns); the tile's last partial group
+// goes one particle per lane. (With ten f64 attributes the vector values
+// raised the kernel from 126 to 194 registers and the 9 x 10 pass from
+// 4.48 to 5.08 ms, so larger counts load one particle per lane.)
 template <typename T, int K>
 __device__ __forceinline__ void multi_tile(const MultiSpec& sp, const Binner<T>& binner, int64_t i0,
                                            int64_t i1) {
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::N;
+    constexpr int KC = K > 0 ? K : (K == 0 ? 1 : kMaxAttr);
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = threadIdx.x & ~31;
     const T* __restrict__ X = static_cast<const T*>(sp.x);
     const T* __restrict__ Y = static_cast<const T*>(sp.y);
     const int A = K >= 0 ? K : sp.n_attrs;
     const bool agg = sp.aggregate != 0;
+    constexpr bool kVec = K >= 0 && K <= 4;
+    bool vec = kVec && ((uintptr_t)X & 15) == 0 && ((uintptr_t)Y & 15) == 0 && i0 % VN == 0;
+    if constexpr (K > 0) {
+#pragma unroll
+        for (int a = 0; a < K; ++a) vec = vec && ((uintptr_t)sp.a[a] & 15) == 0;
+    }
+    int64_t s0 = i0;  // first particle of the scalar part
+    if constexpr (kVec) {
+        if (vec) {
+            const int64_t g0 = i0 / VN, g1 = i1 / VN;
+            const V* XV = reinterpret_cast<const V*>(X);
+            const V* YV = reinterpret_cast<const V*>(Y);
+            for (int64_t base = g0 + warp0; base < g1; base += blockDim.x) {
+                const int64_t gi = base + lane;
+                const bool live = gi < g1;
+                V xv, yv, av[KC];
+                if (live) {
+                    xv = __ldg(XV + gi);
+                    yv = __ldg(YV + gi);
+                    if constexpr (K > 0) {
+    #pragma unroll
+                        for (int a = 0; a < K; ++a) av[a] = __ldg(reinterpret_cast<const V*>(sp.a[a]) + gi);
+                    }
+                }
+    #pragma unroll
+                for (int j = 0; j < VN; ++j) {
+                    int b = -1;
+                    T v[KC];
+                    if (live) {
+                        b = binner.bin(vget<T>(xv, j), vget<T>(yv, j));
+                        if constexpr (K > 0) {
+    #pragma unroll
+                            for (int a = 0; a < K; ++a) v[a] = vget<T>(av[a], j);
+                        }
+                    }
+                    warp_commit<T, K>(sp.st, A, b, v, agg);
+                }
+            }
+            s0 = g1 * VN;
+        }
+    }
     // whole warps iterate together (warp_commit needs every lane)
-    for (int64_t base = i0 + warp0; base < i1; base += blockDim.x) {
+    for (int64_t base = s0 + warp0; base < i1; base += blockDim.x) {
         const int64_t i = base + lane;
         int b = -1;
-        T v[K > 0 ? K : (K == 0 ? 1 : kMaxAttr)];
+        T v[KC];
         if (i < i1) {
             b = binner.bin(X[i], Y[i]);
             if constexpr (K > 0) {
