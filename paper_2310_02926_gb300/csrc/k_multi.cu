@@ -163,9 +163,11 @@ cudaError_t launch_bin_multi(const KernelCtx& kc, int dtype, const MultiSpec* de
                              const int* group_attrs, const int* group_size, int n_groups, int64_t n) {
     if (n <= 0 || n_groups <= 0) return cudaSuccess;
     int64_t grid = (n + kMultiTile - 1) / kMultiTile;
-    // 4 CTAs per SM: a tile's columns (kMultiTile x columns x 8 B) stay within
-    // a CTA's share of L2 between the specs that read them
-    const int64_t cap = (int64_t)kc.num_sms * 4;
+    // 2 CTAs per SM: a tile's columns (kMultiTile x columns x 8 B) stay within
+    // a CTA's share of L2 between the specs that read them (measured at 2^22
+    // f64 particles, 13 columns: 1, 2 and 4 CTAs per SM took 5.14, 4.43 and
+    // 4.45 ms for 9 x 10 binnings on 256^2 meshes)
+    const int64_t cap = (int64_t)kc.num_sms * 2;
     if (grid > cap) grid = cap;
     const MultiSpec* p = dev_specs;
     for (int g = 0; g < n_groups; ++g) {
