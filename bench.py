@@ -634,6 +634,27 @@ def run_serving(args, n_requests):
     return line
 
 
+def host_link_gbs(dev, nbytes: int = 1 << 30, reps: int = 5):
+    """Page-locked host <-> device copy rates (GB/s, best of reps)."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        best = None
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            dst.copy_(src, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None or ms < best else best
+        out[name] = nbytes / (best / 1e3) / 1e9
+    del h, d
+    return out
+
+
 def time_threaded_baseline(w, min_seconds: float, max_reps: int):
     """The all-core CPU baseline (oracle/binning_threaded.c) on the whole
     workload: particles/s and the threads it used."""
@@ -761,8 +782,17 @@ def run_single(args, name, n, env, with_e2e=True, with_cpu=True, check=False, st
             ctx.bin_particles(hcols[0], hcols[1], hcols[2:], w.lo, w.hi, w.res, ops=ops, out=hout)
         t_e2e = (time.perf_counter() - t0) / args.e2e_steps
         bn.bn_context_profile(ctx.handle)
+        link = host_link_gbs(dev)
+        moved = (bytes_in + bytes_out) / t_e2e / 1e9
+        # the host link bounds end to end: the inputs cross it once (read in
+        # place from page-locked memory) and the outputs once
+        bound_s = bytes_in / (link["h2d_gbs"] * 1e9) + bytes_out / (link["d2h_gbs"] * 1e9)
         e2e = {"value": n / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_in,
-               "d2h_bytes_per_step": bytes_out, "ms_per_step": 1e3 * t_e2e}
+               "d2h_bytes_per_step": bytes_out, "ms_per_step": 1e3 * t_e2e,
+               "roofline": {"bound": "host link", "achieved_gbs": moved, "host_link": link,
+                            "frac": bound_s / t_e2e,
+                            "note": "frac = (h2d bytes / h2d copy rate + d2h bytes / d2h copy rate) / "
+                                    "e2e step time; rates are page-locked cudaMemcpy copies of 1 GiB"}}
 
     errors = None
     if check and rank == 0:
