@@ -6,7 +6,9 @@
 // (k_batch.cu) between one init/edge launch and one finalise launch. The
 // launches are captured once per plan shape in a CUDA graph; a later batch
 // with the same shape (block sizes, meshes, strategies) only rewrites the
-// block descriptors in pinned memory and replays the graph.
+// block descriptors, and the arguments of the blocks on the sort path, in
+// pinned memory and replays the graph (its copy nodes move them to the
+// device; the sort blocks' scratch lives in the plan's memory).
 //
 // Autotuner: blocks fall into shape classes (dtype, attributes, ops, log2
 // of the bin count, log2 of the particle count). The first block of a new
@@ -61,11 +63,21 @@ struct BatchGraph {
     BatchBlock* d_blocks = nullptr;
     cudaEvent_t last = nullptr;  // completion of the last replay (pinned buffer reuse)
     uint64_t launches = 0;       // kernels per replay
+    // blocks on the sort path: their scratch and a device copy of their
+    // arguments (sort_dev), rewritten from sort_args before every replay, so
+    // the captured kernels' parameters stay the same from call to call
+    void* sort_dev = nullptr;
+    BinArgs* sort_args = nullptr;  // pinned, one per sort block
+    size_t sort_args_off = 0;
+    std::vector<size_t> sort_off;
+    std::vector<SortDesc> sort_sd;
     ~BatchGraph() {
         if (last) cudaEventSynchronize(last), cudaEventDestroy(last);
         if (exec) cudaGraphExecDestroy(exec);
         if (dev) cudaFree(dev);
         if (host) cudaFreeHost(host);
+        if (sort_dev) cudaFree(sort_dev);
+        if (sort_args) cudaFreeHost(sort_args);
     }
 };
 
@@ -528,22 +540,33 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
         }
     }
 
-    // blocks on the sort path: their scratch and arguments change per call
-    struct SortJob {
-        BinArgs a;
-        SortDesc sd;
-        void* scratch;
-    };
-    std::vector<SortJob> sorts;
-    for (const FastBlock& f : fbs) {
-        if (f.bb.strategy != BN_STRATEGY_SORT || f.bb.n == 0) continue;
-        SortJob j;
-        j.a = sort_args(f, dtype, A, sum_mode);
-        if (!sort_plan(j.a, c->smem_optin, &j.sd)) return fail(BN_ERR_INTERNAL, "bn_bin_batch: sort plan changed");
-        j.scratch = plan.alloc(sort_scratch_bytes(j.sd, j.a));
-        if (!j.scratch) return cuda_fail(plan.err, "bn_bin_batch: sort scratch");
-        sorts.push_back(j);
+    // blocks on the sort path: scratch and argument copies in the plan's own
+    // memory (sized once per plan shape), arguments rewritten every call
+    std::vector<const FastBlock*> sort_blocks;
+    for (const FastBlock& f : fbs)
+        if (f.bb.strategy == BN_STRATEGY_SORT && f.bb.n > 0) sort_blocks.push_back(&f);
+    const size_t n_sorts = sort_blocks.size();
+    if (n_sorts && !G->sort_dev) {
+        size_t off = 0;
+        for (const FastBlock* f : sort_blocks) {
+            const BinArgs a = sort_args(*f, dtype, A, sum_mode);
+            SortDesc sd;
+            if (!sort_plan(a, c->smem_optin, &sd)) return fail(BN_ERR_INTERNAL, "bn_bin_batch: no sort plan");
+            G->sort_sd.push_back(sd);
+            G->sort_off.push_back(off);
+            off += align256(sort_scratch_bytes(sd, a));
+        }
+        G->sort_args_off = off;
+        off += align256(sizeof(BinArgs) * n_sorts);
+        cudaError_t e = cudaMalloc(&G->sort_dev, off);
+        if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&G->sort_args), sizeof(BinArgs) * n_sorts,
+                                                cudaHostAllocDefault);
+        if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: sort plan memory");
     }
+    // the previous replay has released the pinned copies (G->last waited above)
+    for (size_t j = 0; j < n_sorts; ++j) G->sort_args[j] = sort_args(*sort_blocks[j], dtype, A, sum_mode);
+    unsigned char* sdev = static_cast<unsigned char*>(G->sort_dev);
+    BinArgs* d_sort_args = n_sorts ? reinterpret_cast<BinArgs*>(sdev + G->sort_args_off) : nullptr;
 
     unsigned char* d = static_cast<unsigned char*>(G->dev);
     std::atomic<uint64_t> nlaunch{0};
@@ -556,8 +579,11 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
                              reinterpret_cast<int64_t*>(d + L.off_edge_start),
                              reinterpret_cast<int4*>(d + L.off_items), reinterpret_cast<int*>(d + L.off_counter),
                              n_blocks, ni, bins, edges, smem, false);
-        for (SortJob& j : sorts)
-            if (e2 == cudaSuccess) e2 = launch_bin_sort(kc, j.a, j.sd, j.scratch);
+        if (e2 == cudaSuccess && n_sorts)
+            e2 = cudaMemcpyAsync(d_sort_args, G->sort_args, sizeof(BinArgs) * n_sorts, cudaMemcpyHostToDevice,
+                                 c->stream);
+        for (size_t j = 0; j < n_sorts && e2 == cudaSuccess; ++j)
+            e2 = launch_bin_sort(kc, G->sort_args[j], G->sort_sd[j], sdev + G->sort_off[j], d_sort_args + j);
         if (e2 == cudaSuccess && want_avg)
             e2 = launch_batch_finalize(kc, G->d_blocks, reinterpret_cast<int64_t*>(d + L.off_bin_start), n_blocks, bins);
         return e2;
@@ -571,24 +597,16 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
         cudaEventRecord(G->last, c->stream);
         return BN_OK;
     }
-    if (!G->exec || !sorts.empty()) {
-        // capture; a graph with sort blocks is re-captured every call (their
-        // kernel arguments carry this call's pointers) and the executable
-        // graph updated in place
+    if (!G->exec) {
+        // capture once per plan shape: every per-call value (block
+        // descriptors, sort arguments) reaches the kernels through the plan's
+        // memory, which the graph's copy nodes rewrite from pinned buffers
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
         cudaError_t eb = e == cudaSuccess ? body() : e;
         cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
         if (e == cudaSuccess) e = eb != cudaSuccess ? eb : ee;
-        if (e == cudaSuccess && G->exec) {
-            cudaGraphExecUpdateResultInfo info;
-            if (cudaGraphExecUpdate(G->exec, graph, &info) != cudaSuccess) {
-                cudaGetLastError();
-                cudaGraphExecDestroy(G->exec);
-                G->exec = nullptr;
-            }
-        }
-        if (e == cudaSuccess && !G->exec) e = cudaGraphInstantiate(&G->exec, graph, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&G->exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: graph capture");
         G->launches = nlaunch.load();

@@ -85,7 +85,10 @@ struct SortDesc {
 
 bool sort_plan(const BinArgs& a, int smem_optin, SortDesc* sd);
 size_t sort_scratch_bytes(const SortDesc& sd, const BinArgs& a);
-cudaError_t launch_bin_sort(const KernelCtx& kc, const BinArgs& a, SortDesc sd, void* scratch);
+// dargs (may be null): a device copy of `a` the kernels read instead of their
+// by-value arguments (a, sd still give the launch shape and the scratch).
+cudaError_t launch_bin_sort(const KernelCtx& kc, const BinArgs& a, SortDesc sd, void* scratch,
+                            const BinArgs* dargs = nullptr);
 
 // One block of a batch as the persistent kernel sees it (k_batch.cu).
 struct BatchBlock {

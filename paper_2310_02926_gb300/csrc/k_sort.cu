@@ -69,7 +69,11 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int* 
 // faster on GB300 than combining a warp's lanes with __match_any_sync
 // first, even on clustered data).
 template <typename T>
-__global__ void __launch_bounds__(512) k_sort_count(BinArgs args, SortDesc sd) {
+// The kernels taking BinArgs read them from dargs when it is set (a batch
+// plan's device copy, rewritten before every replay of its CUDA graph, so
+// that the graph's kernel parameters do not change from call to call).
+__global__ void __launch_bounds__(512) k_sort_count(BinArgs args_v, SortDesc sd, const BinArgs* dargs) {
+    const BinArgs& args = dargs ? *dargs : args_v;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned* hist = reinterpret_cast<unsigned*>(smem);  // NB
     const GridDesc g = args.dev_grid ? *args.dev_grid : args.grid;
@@ -155,7 +159,8 @@ __global__ void k_sort_plan(SortDesc sd) {
 // (bucket, local bin, rank) per particle. The sorted records then go out to
 // their reserved runs.
 template <typename T, int A_CT, int PER>
-__global__ void __launch_bounds__(1024) k_sort_scatter(BinArgs args, SortDesc sd) {
+__global__ void __launch_bounds__(1024) k_sort_scatter(BinArgs args_v, SortDesc sd, const BinArgs* dargs) {
+    const BinArgs& args = dargs ? *dargs : args_v;
     extern __shared__ __align__(16) unsigned char smem[];
     const GridDesc g = args.dev_grid ? *args.dev_grid : args.grid;
     if (!g.valid) return;
@@ -282,7 +287,8 @@ __global__ void __launch_bounds__(1024) k_sort_scatter(BinArgs args, SortDesc sd
 // Persistent CTAs take work items; an item's records are consecutive slots,
 // streamed U per thread per step (all loads first).
 template <typename T, int A_CT, int MODE>
-__global__ void __launch_bounds__(1024) k_sort_reduce(BinArgs args, SortDesc sd) {
+__global__ void __launch_bounds__(1024) k_sort_reduce(BinArgs args_v, SortDesc sd, const BinArgs* dargs) {
+    const BinArgs& args = dargs ? *dargs : args_v;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
     const int A = A_CT >= 0 ? A_CT : args.n_attrs;
@@ -402,7 +408,8 @@ size_t sort_scratch_bytes(const SortDesc& sd, const BinArgs& a) {
 }
 
 template <typename T, int A_CT, int MODE>
-static cudaError_t launch_sort_t(const KernelCtx& kc, const BinArgs& a, const SortDesc& sd) {
+static cudaError_t launch_sort_t(const KernelCtx& kc, const BinArgs& a, const SortDesc& sd,
+                                 const BinArgs* dargs) {
     auto scat = sd.per == 16 ? k_sort_scatter<T, A_CT, 16> : k_sort_scatter<T, A_CT, 8>;
     auto red = k_sort_reduce<T, A_CT, MODE>;
     auto cnt = k_sort_count<T>;
@@ -417,32 +424,34 @@ static cudaError_t launch_sort_t(const KernelCtx& kc, const BinArgs& a, const So
     const int64_t cwant = (a.n + 512 * 4 - 1) / (512 * 4);
     if (cgrid > cwant) cgrid = cwant;
     if (cgrid < 1) cgrid = 1;
-    cnt<<<(unsigned)cgrid, 512, sd.smem_count, kc.stream>>>(a, sd);
+    cnt<<<(unsigned)cgrid, 512, sd.smem_count, kc.stream>>>(a, sd, dargs);
     k_sort_plan<<<1, 1024, 0, kc.stream>>>(sd);
-    scat<<<(unsigned)sd.tiles, sd.tp / sd.per, sd.smem_scatter, kc.stream>>>(a, sd);
+    scat<<<(unsigned)sd.tiles, sd.tp / sd.per, sd.smem_scatter, kc.stream>>>(a, sd, dargs);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, red, 1024, sd.smem_reduce);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)kc.num_sms * per_sm;
     if (grid > sd.max_items) grid = sd.max_items;
-    red<<<(unsigned)grid, 1024, sd.smem_reduce, kc.stream>>>(a, sd);
+    red<<<(unsigned)grid, 1024, sd.smem_reduce, kc.stream>>>(a, sd, dargs);
     kc.count_launch(4);
     return cudaGetLastError();
 }
 
 template <typename T, int MODE>
-static cudaError_t dispatch_sort(const KernelCtx& kc, const BinArgs& a, const SortDesc& sd) {
+static cudaError_t dispatch_sort(const KernelCtx& kc, const BinArgs& a, const SortDesc& sd,
+                                 const BinArgs* dargs) {
     switch (a.n_attrs) {
-        case 0: return launch_sort_t<T, 0, MODE>(kc, a, sd);
-        case 1: return launch_sort_t<T, 1, MODE>(kc, a, sd);
-        case 2: return launch_sort_t<T, 2, MODE>(kc, a, sd);
-        case 3: return launch_sort_t<T, 3, MODE>(kc, a, sd);
-        case 4: return launch_sort_t<T, 4, MODE>(kc, a, sd);
-        default: return launch_sort_t<T, -1, MODE>(kc, a, sd);
+        case 0: return launch_sort_t<T, 0, MODE>(kc, a, sd, dargs);
+        case 1: return launch_sort_t<T, 1, MODE>(kc, a, sd, dargs);
+        case 2: return launch_sort_t<T, 2, MODE>(kc, a, sd, dargs);
+        case 3: return launch_sort_t<T, 3, MODE>(kc, a, sd, dargs);
+        case 4: return launch_sort_t<T, 4, MODE>(kc, a, sd, dargs);
+        default: return launch_sort_t<T, -1, MODE>(kc, a, sd, dargs);
     }
 }
 
-cudaError_t launch_bin_sort(const KernelCtx& kc, const BinArgs& a, SortDesc sd, void* scratch) {
+cudaError_t launch_bin_sort(const KernelCtx& kc, const BinArgs& a, SortDesc sd, void* scratch,
+                            const BinArgs* dargs) {
     const size_t tsz = a.dtype == BN_F64 ? 8 : 4;
     unsigned char* p = static_cast<unsigned char*>(scratch);
     sd.keys = reinterpret_cast<unsigned short*>(p);
@@ -459,11 +468,11 @@ cudaError_t launch_bin_sort(const KernelCtx& kc, const BinArgs& a, SortDesc sd, 
     cudaError_t e = cudaMemsetAsync(sd.bucket_total, 0, (size_t)sd.nb * 4, kc.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(sd.counters, 0, 256, kc.stream);
     if (e != cudaSuccess) return e;
-    if (a.dtype == BN_F64) return dispatch_sort<double, kSumF64>(kc, a, sd);
+    if (a.dtype == BN_F64) return dispatch_sort<double, kSumF64>(kc, a, sd, dargs);
     switch (a.sum_mode) {
-        case kSumF32: return dispatch_sort<float, kSumF32>(kc, a, sd);
-        case kSumF64: return dispatch_sort<float, kSumF64>(kc, a, sd);
-        default: return dispatch_sort<float, kSumF32C>(kc, a, sd);
+        case kSumF32: return dispatch_sort<float, kSumF32>(kc, a, sd, dargs);
+        case kSumF64: return dispatch_sort<float, kSumF64>(kc, a, sd, dargs);
+        default: return dispatch_sort<float, kSumF32C>(kc, a, sd, dargs);
     }
 }
 
