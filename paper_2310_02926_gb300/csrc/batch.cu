@@ -109,9 +109,11 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int64_t choose_tile(int strategy, int64_t n, int64_t bins, int num_sms) {
     if (strategy == BN_STRATEGY_PRIVATE) {
         // at least 8 particles per bin so clearing and merging the mesh is
-        // amortised, at least 32K, and no more items than 2 per SM need
+        // amortised, at least 32K, and no more items than 2 per SM need;
+        // at most kLimbMaxAdds (the most one limb-sum mesh may take per bin)
         int64_t t = std::max<int64_t>(8 * bins, 32768);
         t = std::max<int64_t>(t, (n + 2 * num_sms - 1) / (2 * num_sms));
+        t = std::min<int64_t>(t, kLimbMaxAdds);
         return std::min<int64_t>(t, std::max<int64_t>(n, 1));
     }
     int64_t t = (n + 4 * num_sms - 1) / (4 * num_sms);

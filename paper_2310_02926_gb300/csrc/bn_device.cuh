@@ -218,10 +218,27 @@ __device__ __forceinline__ void add96(unsigned long long* lo, int* hi, long long
 // filter. Half the shared-memory bytes per particle for min/max, and the
 // mesh leaves more room; data with many values tied at a bin's extreme pays
 // one L2 reduction per tied particle instead.
+//
+// MODE kSumLimbs (f32 only): each sum is an exact integer in three 32-bit
+// limbs ([A][3][B]), updated with native 32-bit integer atomics only (on
+// GB300 FP32 and 64-bit shared-memory adds are emulated, and on one hot bin
+// they fall to a few percent of the integer rate). Per attribute the mesh
+// takes a window of 24 binades whose top lies two binades above the largest
+// exponent in a sample of the values it will see (sample(), before the
+// first add); a value v = +-m 2^(e-150) in the window is the integer
+// q = +-m 2^sh, sh = e + 23 - top in [0, 23], so |q| < 2^47 and q = d0 +
+// d1 2^16 + d2 2^32 with 16-bit digits d0, d1 >= 0 and a signed d2; the
+// limbs add up the digits (zero digits are skipped). With at most
+// kLimbMaxAdds values per bin the limbs cannot overflow, and the bin's sum
+// is exact until it is rounded once to FP64 in the merge. A value outside
+// the window (or 0 < |v| < 2^-126, inf, NaN) is added to the global FP64
+// sum directly.
 template <typename T, int MODE>
 struct SmemMesh {
     static constexpr bool kWide = sizeof(T) == 8 || MODE == kSumF64 || MODE == kSumF64Keys;
     static constexpr bool kGK = MODE == kSumF64Keys;
+    static constexpr bool kLimbs = MODE == kSumLimbs;
+    static_assert(!kLimbs || sizeof(T) == 4, "limb sums take f32 values");
     using KO = KeyOf<T>;
     using K = typename KO::K;
     using K2 = typename KO::K2;
@@ -232,9 +249,46 @@ struct SmemMesh {
     K2* mm;  // [A][B] {min key, max key}
     int2* flt;  // kGK: [B][A] {top 32 bits of min key, of max key}
     K2* gkeys;  // kGK: the global key records, gk_rp pairs per bin
+    unsigned* lb;          // kLimbs: [A][3][B] digit sums (limb 2 signed)
+    int* lexp;             // kLimbs: [A] largest sampled biased exponent
+    int* lfb;              // kLimbs: set once a value went to the FP64 sums
+    double* const* fsum;   // kLimbs: the global FP64 sums (StateDesc::sum)
+    int64_t fbase;         // kLimbs: global bin of local bin 0
     int gk_rp, n_a;
     int B;
     bool do_sum, do_mm, do_min, do_max;
+
+    // kLimbs: where values outside the window go (the global sums of the
+    // bins this mesh covers, local bin l being global bin base + l).
+    __device__ void bind_fallback(double* const* sums, int64_t base) {
+        fsum = sums;
+        fbase = base;
+    }
+
+    // kLimbs: let value v of attribute a into the sample that sets the
+    // window (any thread, between clear() and the barrier before the first
+    // add; values of other modes are ignored).
+    __device__ __forceinline__ void sample(int a, T v) {
+        if constexpr (kLimbs) {
+            const int e = (int)(__float_as_uint(v) >> 23) & 0xff;
+            if (e > 0 && e < 0xff) atomicMax(&lexp[a], e);
+        }
+    }
+
+    // kLimbs: the window's top exponent (two binades above the sampled
+    // maximum; that of 4.0 with no sample).
+    __device__ __forceinline__ int limb_top(int a) const {
+        const int e = lexp[a];
+        return (e > 0 ? e : 127) + 2;
+    }
+
+    // kLimbs: the exact sum of local bin b's limbs, rounded once to FP64.
+    __device__ __forceinline__ double limb_value(int a, int b) const {
+        const unsigned* L = lb + (size_t)a * 3 * B + b;
+        const double hi = (double)(int)L[2 * B] * 4294967296.0;
+        const double lo = (double)((unsigned long long)L[B] * 65536ull + L[0]);
+        return __dmul_rn(__dadd_rn(hi, lo), pow2(limb_top(a) - 173));
+    }
 
     __device__ void bind_keys(const StateDesc& st) {
         gkeys = static_cast<K2*>(st.mmk);
@@ -252,7 +306,15 @@ struct SmemMesh {
         s64 = nullptr;
         s32 = nullptr;
         c32 = nullptr;
-        if (do_sum) {
+        lb = nullptr;
+        lexp = nullptr;
+        lfb = nullptr;
+        fsum = nullptr;
+        fbase = 0;
+        if (do_sum && kLimbs) {
+            lb = reinterpret_cast<unsigned*>(base + off);
+            off += (size_t)A * 3 * B * 4;
+        } else if (do_sum) {
             if (kWide) {
                 s64 = reinterpret_cast<double*>(base + off);
                 off += (size_t)A * B * 8;
@@ -269,6 +331,12 @@ struct SmemMesh {
         n_a = A;
         mm = (do_mm && !kGK) ? reinterpret_cast<K2*>(base + off) : nullptr;
         flt = (do_mm && kGK) ? reinterpret_cast<int2*>(base + off) : nullptr;
+        if (do_mm) off += (size_t)A * B * (kGK ? 8 : sizeof(K2));
+        if (kLimbs) {  // [A] sampled exponents, then the fallback flag
+            off = (off + 15) & ~(size_t)15;
+            lexp = reinterpret_cast<int*>(base + off);
+            lfb = lexp + A;
+        }
         gkeys = nullptr;
         gk_rp = 0;
     }
@@ -276,7 +344,11 @@ struct SmemMesh {
     __device__ void clear(int A) {
         for (int b = threadIdx.x; b < B; b += blockDim.x) cnt[b] = 0u;
         const int AB = A * B;
-        if (do_sum) {
+        if (kLimbs) {
+            if (do_sum)
+                for (int k = threadIdx.x; k < 3 * AB; k += blockDim.x) lb[k] = 0u;
+            for (int k = threadIdx.x; k <= A; k += blockDim.x) lexp[k] = 0;  // and the flag
+        } else if (do_sum) {
             if (kWide) {
                 for (int k = threadIdx.x; k < AB; k += blockDim.x) s64[k] = 0.0;
             } else {
@@ -299,7 +371,24 @@ struct SmemMesh {
 
     __device__ __forceinline__ void add(int a, int b, T v) {
         const int k = a * B + b;
-        if (do_sum) {
+        if (do_sum && kLimbs) {
+            const unsigned u = __float_as_uint((float)v);
+            const int e = (int)(u >> 23) & 0xff;
+            const int sh = e + 23 - limb_top(a);
+            if (e > 0 && e < 0xff && sh >= 0 && sh <= 23) {
+                const unsigned long long mag = (unsigned long long)((u & 0x7fffffu) | 0x800000u) << sh;
+                const long long q = (u >> 31) ? -(long long)mag : (long long)mag;
+                const unsigned d0 = (unsigned)q & 0xffffu, d1 = (unsigned)q >> 16;
+                const int d2 = (int)(q >> 32);
+                unsigned* L = lb + (size_t)a * 3 * B + b;
+                if (d0) atomicAdd(L, d0);
+                if (d1) atomicAdd(L + B, d1);
+                if (d2) atomicAdd(reinterpret_cast<int*>(L + 2 * B), d2);
+            } else if ((u << 1) != 0u) {  // +-0 adds nothing
+                atomicAdd(fsum[a] + fbase + b, (double)v);
+                *lfb = 1;
+            }
+        } else if (do_sum) {
             if (kWide) {
                 atomicAdd(&s64[k], (double)v);
             } else if (MODE == kSumF32) {
@@ -396,6 +485,7 @@ struct SmemMesh {
     // Sum of one bin as FP64: the FP64 accumulator, the FP32 partial, or the
     // FP32 partial plus its compensation term (unless the partial is inf/NaN).
     __device__ __forceinline__ double sum_value(int k) const {
+        if (kLimbs) return limb_value(k / B, k % B);
         if (kWide) return s64[k];
         if (MODE == kSumF32) return (double)s32[k];
         const float hi = s32[k];
@@ -418,7 +508,17 @@ struct SmemMesh {
                 st.count[b] = (unsigned long long)c;
                 for (int a = 0; a < A; ++a) {
                     const int k = a * B + l;
-                    if (do_sum) st.sum[a][b] = sum_value(k);
+                    if (do_sum) {
+                        if (kLimbs) {
+                            // the global sum holds the values that went
+                            // around the limbs (zero when none did)
+                            double v = c ? limb_value(a, l) : 0.0;
+                            if (c && *lfb) v = __dadd_rn(v, __ldcg(&st.sum[a][b]));
+                            st.sum[a][b] = v;
+                        } else {
+                            st.sum[a][b] = sum_value(k);
+                        }
+                    }
                     if (do_mm && !kGK) {
                         const K2 cur = mm[k];
                         if (st.mmk) {
@@ -435,7 +535,7 @@ struct SmemMesh {
             atomicAdd(&st.count[b], (unsigned long long)c);
             for (int a = 0; a < A; ++a) {
                 const int k = a * B + l;
-                if (do_sum) atomicAdd(&st.sum[a][b], sum_value(k));
+                if (do_sum) atomicAdd(&st.sum[a][b], kLimbs ? limb_value(a, l) : sum_value(k));
                 if (kGK) continue;  // min/max already in the global key records
                 if (do_mm && st.mmk) {
                     const K2 cur = mm[k];

@@ -111,6 +111,15 @@ __global__ void __launch_bounds__(1024) k_batch_bin(const BatchBlock* blocks, co
             m.carve(smem, B, A, bb.st.do_sum != 0, bb.st.do_min != 0, bb.st.do_max != 0);
             m.clear(A);
             __syncthreads();
+            if (MODE == kSumLimbs && bb.st.do_sum) {
+                // the window of the limb sums: the item's first particles
+                // (an item holds at most kLimbMaxAdds particles)
+                const int64_t i = p0 + threadIdx.x;
+                if (i < p1)
+                    for (int a = 0; a < A; ++a) m.sample(a, acol[a][i]);
+                m.bind_fallback(bb.st.sum, 0);
+                __syncthreads();
+            }
             // coalesced scalar loads, four particles in flight per thread
             const int64_t step = blockDim.x;
             int64_t i = p0 + threadIdx.x;
@@ -239,11 +248,9 @@ static cudaError_t dispatch_batch(const KernelCtx& kc, const BatchBlock* blocks,
 cudaError_t launch_batch_bin(const KernelCtx& kc, int dtype, int sum_mode, const BatchBlock* blocks,
                              const int4* items, int n_items, int* counter, int n_attrs, size_t smem) {
     if (dtype == BN_F64) return dispatch_batch<double, kSumF64>(kc, blocks, items, n_items, counter, n_attrs, smem);
-    switch (sum_mode) {
-        case kSumF32: return dispatch_batch<float, kSumF32>(kc, blocks, items, n_items, counter, n_attrs, smem);
-        case kSumF64: return dispatch_batch<float, kSumF64>(kc, blocks, items, n_items, counter, n_attrs, smem);
-        default: return dispatch_batch<float, kSumF32C>(kc, blocks, items, n_items, counter, n_attrs, smem);
-    }
+    if (smem_sum_mode(dtype, sum_mode) == kSumF32)
+        return dispatch_batch<float, kSumF32>(kc, blocks, items, n_items, counter, n_attrs, smem);
+    return dispatch_batch<float, kSumLimbs>(kc, blocks, items, n_items, counter, n_attrs, smem);
 }
 
 }  // namespace bn

@@ -25,7 +25,8 @@ namespace bn {
 // room for one CTA only, so that an SM still has 32 warps to hide the
 // shared-memory atomic latency with.
 template <typename T, int A_CT, int MODE, int NT>
-__global__ void __launch_bounds__(NT, 1) k_bin_private(BinArgs args, int64_t head, int64_t groups) {
+__global__ void __launch_bounds__(NT, 1) k_bin_private(const __grid_constant__ BinArgs args, int64_t head,
+                                                       int64_t groups) {
     extern __shared__ __align__(16) unsigned char smem[];
     using V = typename VecOf<T>::type;
     constexpr int VN = VecOf<T>::N;
@@ -42,6 +43,17 @@ __global__ void __launch_bounds__(NT, 1) k_bin_private(BinArgs args, int64_t hea
     Binner<T> binner;
     binner.init(g);
     __syncthreads();
+    if (MODE == kSumLimbs && st.do_sum) {
+        // the window of the limb sums: one value per thread and attribute
+        const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (i < args.n)
+            for (int a = 0; a < A; ++a) {
+                const int64_t sa = args.sa[a] > 1 ? args.sa[a] : 1;
+                m.sample(a, static_cast<const T*>(args.a[a])[i * sa]);
+            }
+        m.bind_fallback(st.sum, 0);
+        __syncthreads();
+    }
 
     const T* __restrict__ X = static_cast<const T*>(args.x);
     const T* __restrict__ Y = static_cast<const T*>(args.y);
@@ -161,22 +173,23 @@ static size_t private_bytes_for(int dtype, int mode, int B, int A, bool s, bool 
     const bool wide = dtype == BN_F64 || mode == kSumF64 || mode == kSumF64Keys;
     const size_t tsz = dtype == BN_F64 ? 8 : 4;
     size_t b = ((size_t)B * 4 + 15) & ~(size_t)15;
-    if (s) b += (size_t)A * B * (wide ? 8 : (mode == kSumF32C ? 8 : 4));
+    if (s) b += (size_t)A * B * (mode == kSumLimbs ? 12 : wide ? 8 : (mode == kSumF32C ? 8 : 4));
     b = (b + 15) & ~(size_t)15;
     // {min key, max key}, or their top 32 bits as a filter (kSumF64Keys)
     if (lo || hi) b += (size_t)A * B * (mode == kSumF64Keys ? 8 : 2 * tsz);
+    if (mode == kSumLimbs) b = ((b + 15) & ~(size_t)15) + (size_t)(A + 1) * 4;  // exponents, flag
     return b;
 }
 
 // The mesh mode a particle pass uses: f64 min/max go through the global key
 // records when the runtime provides them.
 static int private_mode(const BinArgs& a) {
-    if (a.dtype != BN_F64) return a.sum_mode;
+    if (a.dtype != BN_F64) return smem_sum_mode(a.dtype, a.sum_mode);
     return (a.st.mmk && (a.st.do_min || a.st.do_max)) ? kSumF64Keys : kSumF64;
 }
 
 size_t private_mesh_bytes(int dtype, int sum_mode, int64_t bins, int n_attrs, bool s, bool lo, bool hi) {
-    return private_bytes_for(dtype, dtype == BN_F64 ? kSumF64 : sum_mode, (int)bins, n_attrs, s, lo, hi);
+    return private_bytes_for(dtype, smem_sum_mode(dtype, sum_mode), (int)bins, n_attrs, s, lo, hi);
 }
 
 size_t private_smem_bytes(const BinArgs& a, int smem_optin, int keys) {
@@ -224,6 +237,15 @@ static cudaError_t launch_private_t(const KernelCtx& kc, const BinArgs& a, size_
     if (want < 1) want = 1;
     int64_t grid = (int64_t)kc.num_sms * per_sm;
     if (grid > want) grid = want;
+    if (MODE == kSumLimbs) {
+        // a limb mesh takes at most kLimbMaxAdds values per bin: enough CTAs
+        // that none sees more particles (each thread: at most `per` of the
+        // body, one of the head and one of the tail)
+        constexpr int VN = VecOf<T>::N;
+        const int64_t per = kLimbMaxAdds / block - 2 * VN;
+        const int64_t need = (a.n + per * block - 1) / (per * block);
+        if (grid < need) grid = need;
+    }
     if constexpr (A_CT >= 0) {
         if (wide)
             k_bin_private<T, A_CT, MODE, 1024><<<(int)grid, block, smem, kc.stream>>>(a, head, groups);
@@ -251,11 +273,8 @@ cudaError_t launch_bin_private(const KernelCtx& kc, const BinArgs& a) {
     if (a.dtype == BN_F64)
         return private_mode(a) == kSumF64Keys ? dispatch_a<double, kSumF64Keys>(kc, a, smem)
                                               : dispatch_a<double, kSumF64>(kc, a, smem);
-    switch (a.sum_mode) {
-        case kSumF32: return dispatch_a<float, kSumF32>(kc, a, smem);
-        case kSumF64: return dispatch_a<float, kSumF64>(kc, a, smem);
-        default: return dispatch_a<float, kSumF32C>(kc, a, smem);
-    }
+    if (private_mode(a) == kSumF32) return dispatch_a<float, kSumF32>(kc, a, smem);
+    return dispatch_a<float, kSumLimbs>(kc, a, smem);
 }
 
 }  // namespace bn

@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(1024) k_sort_reduce(BinArgs args_v, SortDesc s
     m.carve(smem, BK, A, args.st.do_sum != 0, args.st.do_min != 0, args.st.do_max != 0);
     const unsigned short* __restrict__ keys = sd.keys;
     const T* __restrict__ attrs = static_cast<const T*>(sd.attrs);
+    constexpr bool kLimbs = MODE == kSumLimbs;
 
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&sd.counters[1], 1);
@@ -309,7 +310,15 @@ __global__ void __launch_bounds__(1024) k_sort_reduce(BinArgs args_v, SortDesc s
         if (item >= sd.counters[0]) break;
         const int4 it = sd.items[item];
         m.clear(A);
+        if (kLimbs) m.bind_fallback(args.st.sum, (int64_t)it.x * BK);
         __syncthreads();
+        if (kLimbs && args.st.do_sum) {
+            // the window of the limb sums: the item's first records
+            const int r = it.y + (int)threadIdx.x;
+            if (r < it.z)
+                for (int a = 0; a < A; ++a) m.sample(a, attrs[(int64_t)a * S + r]);
+            __syncthreads();
+        }
         for (int r0 = it.y + threadIdx.x; r0 < it.z; r0 += U * blockDim.x) {
             int l[U];
             T v[U][AC];
@@ -340,9 +349,10 @@ static size_t mesh_bytes(int dtype, int mode, int bins, int A, bool s, bool lo, 
     const bool wide = dtype == BN_F64 || mode == kSumF64;
     const size_t tsz = dtype == BN_F64 ? 8 : 4;
     size_t b = ((size_t)bins * 4 + 15) & ~(size_t)15;
-    if (s) b += (size_t)A * bins * (wide ? 8 : (mode == kSumF32C ? 8 : 4));
+    if (s) b += (size_t)A * bins * (mode == kSumLimbs ? 12 : wide ? 8 : (mode == kSumF32C ? 8 : 4));
     b = (b + 15) & ~(size_t)15;
     if (lo || hi) b += (size_t)A * bins * 2 * tsz;  // {min key, max key}
+    if (mode == kSumLimbs) b = ((b + 15) & ~(size_t)15) + (size_t)(A + 1) * 4;  // exponents, flag
     return b;
 }
 
@@ -352,7 +362,7 @@ bool sort_plan(const BinArgs& a, int smem_optin_total, SortDesc* sd) {
     const int smem_optin = smem_optin_total - 1024;  // room for the kernels' static shared memory
     if (a.n > (int64_t)INT_MAX - (1 << 16)) return false;  // 32-bit record slots
     const int64_t B = (int64_t)a.grid.ax[0].res * a.grid.ax[1].res;
-    const int mode = a.dtype == BN_F64 ? kSumF64 : a.sum_mode;
+    const int mode = smem_sum_mode(a.dtype, a.sum_mode);
     const size_t tsz = a.dtype == BN_F64 ? 8 : 4;
     // largest power-of-two bucket whose shared-memory mesh fits
     int log2bk = 16;
@@ -383,7 +393,7 @@ bool sort_plan(const BinArgs& a, int smem_optin_total, SortDesc* sd) {
     sd->per = tp >= 8192 ? 16 : 8;  // 1024, 512, 512, 256 threads
     sd->tiles = (a.n + tp - 1) / tp;
     sd->slots = a.n > 0 ? a.n : 1;
-    sd->chunk = 1 << 16;
+    sd->chunk = kLimbMaxAdds;  // records per work item; also bounds a limb mesh's adds per bin
     sd->off_gpos = (int)align256((size_t)(nb + 1) * 4);
     sd->off_skey = sd->off_gpos + (int)align256((size_t)nb * 4);
     sd->off_sbk = sd->off_skey + (int)align256((size_t)tp * 2);
@@ -469,11 +479,8 @@ cudaError_t launch_bin_sort(const KernelCtx& kc, const BinArgs& a, SortDesc sd, 
     if (e == cudaSuccess) e = cudaMemsetAsync(sd.counters, 0, 256, kc.stream);
     if (e != cudaSuccess) return e;
     if (a.dtype == BN_F64) return dispatch_sort<double, kSumF64>(kc, a, sd, dargs);
-    switch (a.sum_mode) {
-        case kSumF32: return dispatch_sort<float, kSumF32>(kc, a, sd, dargs);
-        case kSumF64: return dispatch_sort<float, kSumF64>(kc, a, sd, dargs);
-        default: return dispatch_sort<float, kSumF32C>(kc, a, sd, dargs);
-    }
+    if (smem_sum_mode(a.dtype, a.sum_mode) == kSumF32) return dispatch_sort<float, kSumF32>(kc, a, sd, dargs);
+    return dispatch_sort<float, kSumLimbs>(kc, a, sd, dargs);
 }
 
 }  // namespace bn
