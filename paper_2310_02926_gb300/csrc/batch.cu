@@ -51,7 +51,12 @@ struct ClassKey {
 struct Choice {
     int strategy;
     int aggregate;
+    int banded;  // private in mesh bands (blocks whose mesh exceeds shared memory)
 };
+
+// The most bands a private block's mesh is cut into: each band re-reads the
+// tile's coordinates (from L2 after the first band).
+constexpr int kMaxBands = 16;
 
 // Cached graph of one plan shape, with the device and pinned memory it uses.
 struct BatchGraph {
@@ -246,7 +251,11 @@ static void fill_plan(std::vector<FastBlock>& fbs, const PlanLayout& L, unsigned
         const FastBlock& f = fbs[k];
         if (f.bb.n == 0 || f.bb.strategy == BN_STRATEGY_SORT) continue;  // sort blocks: own launches
         const int64_t parts = (f.bb.n + f.bb.tile - 1) / f.bb.tile;
-        for (int64_t j = 0; j < parts; ++j) items[ni++] = make_int4(k, (int)j, 0, 0);
+        const int nb = std::max(f.bb.bands, 1);
+        // a tile's bands next to each other: they run together and read the
+        // tile's coordinates from DRAM once
+        for (int64_t j = 0; j < parts; ++j)
+            for (int band = 0; band < nb; ++band) items[ni++] = make_int4(k, (int)j, band, 0);
     }
     BatchBlock* hb = reinterpret_cast<BatchBlock*>(host + L.off_blocks);
     for (int k = 0; k < nblk; ++k) hb[k] = fbs[k].bb;
@@ -258,7 +267,8 @@ static void fill_plan(std::vector<FastBlock>& fbs, const PlanLayout& L, unsigned
 static int count_items(const std::vector<FastBlock>& fbs) {
     int64_t ni = 0;
     for (const FastBlock& f : fbs)
-        if (f.bb.n > 0 && f.bb.strategy != BN_STRATEGY_SORT) ni += (f.bb.n + f.bb.tile - 1) / f.bb.tile;
+        if (f.bb.n > 0 && f.bb.strategy != BN_STRATEGY_SORT)
+            ni += (f.bb.n + f.bb.tile - 1) / f.bb.tile * std::max(f.bb.bands, 1);
     return (int)ni;
 }
 
@@ -284,10 +294,13 @@ static BinArgs sort_args(const FastBlock& f, int dtype, int n_attrs, int sum_mod
 // Time one block alone with one strategy (autotuner trial), on the context
 // stream; the block's outputs are overwritten (the batch recomputes them).
 static float trial(bn_context* c, FastBlock f, int strategy, int aggregate, int dtype, int sum_mode,
-                   int n_attrs, size_t smem, bool want_avg) {
+                   int n_attrs, size_t smem, bool want_avg, int bands = 1, int band_rows = 0) {
     f.bb.strategy = strategy;
     f.bb.aggregate = aggregate;
-    f.bb.tile = choose_tile(strategy, f.bb.n, f.bins, c->num_sms);
+    f.bb.bands = bands;
+    f.bb.band_rows = band_rows;
+    f.bb.tile = choose_tile(strategy, f.bb.n, bands > 1 ? (int64_t)band_rows * f.bb.g.ax[0].res : f.bins,
+                            c->num_sms);
     std::vector<FastBlock> one{f};
     const int n_items = count_items(one);
     PlanLayout L = layout_for(1, n_items, f.edges);
@@ -340,6 +353,30 @@ static float trial(bn_context* c, FastBlock f, int strategy, int aggregate, int 
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     return ms;
+}
+
+// Mesh bands for a private block whose whole mesh exceeds shared memory:
+// the fewest bands of whole rows that fit, rows spread evenly over them
+// (bands = 0: not even one row fits, or more than kMaxBands are needed).
+struct Bands {
+    int bands, rows;
+    size_t bytes;
+};
+static Bands band_layout(const FastBlock& f, int dtype, int sum_mode, int A, bool s, bool lo, bool hi,
+                         int dyn_limit) {
+    const int rx = f.bb.g.ax[0].res, ry = f.bb.g.ax[1].res;
+    auto bytes = [&](int rows) { return private_mesh_bytes(dtype, sum_mode, (int64_t)rows * rx, A, s, lo, hi); };
+    int fit = 0;
+    for (int lo_r = 1, hi_r = ry; lo_r <= hi_r;) {  // largest row count that fits
+        const int mid = lo_r + (hi_r - lo_r) / 2;
+        if (bytes(mid) <= (size_t)dyn_limit) fit = mid, lo_r = mid + 1;
+        else hi_r = mid - 1;
+    }
+    if (fit == 0) return Bands{0, 0, 0};
+    const int bands = (ry + fit - 1) / fit;
+    if (bands > kMaxBands) return Bands{0, 0, 0};
+    const int rows = (ry + bands - 1) / bands;
+    return Bands{bands, rows, bytes(rows)};
 }
 
 static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks, uint32_t ops,
@@ -418,9 +455,14 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
         FastBlock& f = fbs[k];
         const size_t mesh = private_mesh_bytes(dtype, sum_mode, f.bins, A, f.bb.st.do_sum, want_min, want_max);
         const bool fits = mesh <= (size_t)dyn_limit && f.bins <= (1 << 20);
-        Choice ch{BN_STRATEGY_GLOBAL, f.bins <= 65536 ? 1 : 0};
+        const Bands bl = fits ? Bands{1, f.bb.g.ax[1].res, mesh}
+                              : band_layout(f, dtype, sum_mode, A, f.bb.st.do_sum, want_min, want_max, dyn_limit);
+        const bool bandable = !fits && bl.bands >= 2;
+        Choice ch{BN_STRATEGY_GLOBAL, f.bins <= 65536 ? 1 : 0, 0};
         if (forced == BN_STRATEGY_PRIVATE) {
-            if (!fits) return fail(BN_ERR_INVALID_ARG, "bn_bin_batch: block %d mesh does not fit shared memory", k);
+            if (!fits && !bandable)
+                return fail(BN_ERR_INVALID_ARG, "bn_bin_batch: block %d mesh does not fit shared memory in %d bands",
+                            k, kMaxBands);
             ch.strategy = BN_STRATEGY_PRIVATE;
         } else if (forced == BN_STRATEGY_SORT) {
             SortDesc probe;
@@ -434,7 +476,7 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
             auto it = cache.choices.find(f.cls);
             if (it != cache.choices.end()) {
                 ch = it->second;
-                if (ch.strategy == BN_STRATEGY_PRIVATE && !fits) ch.strategy = BN_STRATEGY_GLOBAL;
+                if (ch.strategy == BN_STRATEGY_PRIVATE && !fits && !bandable) ch.strategy = BN_STRATEGY_GLOBAL;
             } else if (f.bb.n > 0) {
                 float best = -1.0f;
                 SortDesc probe;
@@ -445,18 +487,23 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
                                          {BN_STRATEGY_SORT, 0}};
                 std::string times;
                 for (auto& cd : cands) {
-                    if (cd[0] == BN_STRATEGY_PRIVATE && !fits) continue;
+                    if (cd[0] == BN_STRATEGY_PRIVATE && !fits && !bandable) continue;
                     if (cd[0] == BN_STRATEGY_SORT && !sort_fits) continue;
+                    const bool band = cd[0] == BN_STRATEGY_PRIVATE && !fits;
                     const float ms = trial(c, f, cd[0], cd[1], dtype, sum_mode, A,
-                                           cd[0] == BN_STRATEGY_PRIVATE ? mesh : 0, want_avg);
+                                           cd[0] == BN_STRATEGY_PRIVATE ? bl.bytes : 0, want_avg,
+                                           band ? bl.bands : 1, band ? bl.rows : 0);
                     char tb[64];
-                    snprintf(tb, sizeof tb, " %s%s=%.3fms",
-                             cd[0] == BN_STRATEGY_PRIVATE ? "private" : cd[0] == BN_STRATEGY_SORT ? "sort" : "global",
-                             cd[0] == BN_STRATEGY_GLOBAL && cd[1] ? "+agg" : "", ms);
+                    if (band)
+                        snprintf(tb, sizeof tb, " private[%d bands]=%.3fms", bl.bands, ms);
+                    else
+                        snprintf(tb, sizeof tb, " %s%s=%.3fms",
+                                 cd[0] == BN_STRATEGY_PRIVATE ? "private" : cd[0] == BN_STRATEGY_SORT ? "sort" : "global",
+                                 cd[0] == BN_STRATEGY_GLOBAL && cd[1] ? "+agg" : "", ms);
                     times += tb;
                     if (ms >= 0.0f && (best < 0.0f || ms < best)) {
                         best = ms;
-                        ch = Choice{cd[0], cd[1]};
+                        ch = Choice{cd[0], cd[1], band ? 1 : 0};
                     }
                 }
                 cache.choices[f.cls] = ch;
@@ -465,7 +512,7 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
                          A, f.cls.lb, f.cls.ln);
                 std::lock_guard<std::mutex> lk2(c->tune_mu);
                 c->tune_log.push_back(std::string(head) + times + " -> " +
-                                      (ch.strategy == BN_STRATEGY_PRIVATE ? "private"
+                                      (ch.strategy == BN_STRATEGY_PRIVATE ? (ch.banded ? "private in bands" : "private")
                                        : ch.strategy == BN_STRATEGY_SORT ? "sort"
                                        : ch.aggregate ? "global+agg" : "global"));
             }
@@ -474,8 +521,12 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
         if (agg == BN_AGG_OFF) ch.aggregate = 0;
         f.bb.strategy = ch.strategy;
         f.bb.aggregate = ch.aggregate;
-        f.bb.tile = choose_tile(ch.strategy, f.bb.n, f.bins, c->num_sms);
-        if (ch.strategy == BN_STRATEGY_PRIVATE) smem = std::max(smem, mesh);
+        const bool banded = ch.strategy == BN_STRATEGY_PRIVATE && !fits;
+        f.bb.bands = banded ? bl.bands : 1;
+        f.bb.band_rows = banded ? bl.rows : f.bb.g.ax[1].res;
+        f.bb.tile = choose_tile(ch.strategy, f.bb.n, banded ? (int64_t)bl.rows * f.bb.g.ax[0].res : f.bins,
+                                c->num_sms);
+        if (ch.strategy == BN_STRATEGY_PRIVATE) smem = std::max(smem, banded ? bl.bytes : mesh);
     }
 
     // ---- plan shape and graph
@@ -491,6 +542,7 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
         shape.push_back(f.bb.g.ax[1].res);
         shape.push_back(f.bb.strategy * 2 + f.bb.aggregate);
         shape.push_back(f.bb.tile);
+        shape.push_back(f.bb.bands);
     }
     const int n_items = count_items(fbs);
     int64_t total_edges = 0;

@@ -202,6 +202,23 @@ template <> __device__ __forceinline__ double neg_inf<double>() {
     return __longlong_as_double((long long)0xfff0000000000000ull);
 }
 
+// ---------------------------------------------------------------- average
+// avg = RN(sum / count) for count >= 1 (Sec. 4.2's per-bin average, in
+// FP64). A power-of-two count divides exactly by scaling, so count 1 is the
+// sum itself and count 2^k one FP64 multiplication by 2^-k (rounded once,
+// as the quotient would be); other counts take the FP64 division, which on
+// GB300's narrow FP64 pipe runs at about a quarter of the memory rate
+// (measured 58 G divisions/s) and bounds a finalise pass over many
+// occupied bins.
+__device__ __forceinline__ double bin_average(double sum, unsigned long long count) {
+    if ((count & (count - 1)) == 0ull) {
+        if (count == 1ull) return sum;
+        const int k = 63 - __clzll((long long)count);
+        return __dmul_rn(sum, __longlong_as_double((long long)(1023 - k) << 52));
+    }
+    return __ddiv_rn(sum, (double)count);
+}
+
 // ---------------------------------------------------------------- bin index
 // Axis in the coordinate's own type, prepared once per thread.
 template <typename T>

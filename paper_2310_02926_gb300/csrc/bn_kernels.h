@@ -101,7 +101,11 @@ struct BatchBlock {
     StateDesc st;      // the block's outputs
     int strategy;      // BN_STRATEGY_PRIVATE or BN_STRATEGY_GLOBAL
     int aggregate;
-    int pad[2];
+    // private blocks whose mesh exceeds shared memory: the mesh is cut into
+    // `bands` bands of `band_rows` mesh rows (the last may be shorter), and
+    // every band of every tile is a work item of its own (bands <= 1: whole)
+    int bands;
+    int band_rows;
 };
 
 cudaError_t launch_batch_prepare(const KernelCtx& kc, int dtype, BatchBlock* dev_blocks,

@@ -79,7 +79,7 @@ __global__ void k_exchange_unpack(ExchangeView ex, StateDesc st) {
             if (st.do_sum) st.sum[a][b] = s;
             if (st.do_min) static_cast<T*>(st.mn[a])[b] = from_key64<T>(ex.minkey[k]);
             if (st.do_max) static_cast<T*>(st.mx[a])[b] = from_key64<T>(ex.maxkey[k]);
-            if (st.do_avg) st.avg[a][b] = c ? __ddiv_rn(s, (double)c) : qnan;
+            if (st.do_avg) st.avg[a][b] = c ? bin_average(s, c) : qnan;
         }
     }
 }

@@ -7,7 +7,9 @@
 // particles and chooses a strategy per block (its autotuner). Persistent
 // CTAs pull items from one queue:
 //   private items: clear a shared-memory copy of the block's mesh, stream
-//     the item's particles into it, merge it into the block's outputs;
+//     the item's particles into it, merge it into the block's outputs (a
+//     mesh larger than shared memory is cut into bands of rows, one item per
+//     band and tile, each skipping the particles of other bands);
 //   global items: stream the item's particles straight into the block's
 //     global mesh with (optionally warp-aggregated) atomics.
 // Around it, one launch each initialises all meshes, builds all f64 edge
@@ -61,7 +63,7 @@ __global__ void k_batch_finalize(const BatchBlock* blocks, const int64_t* bin_st
         const int64_t b = i - bin_start[k];
         const unsigned long long c = bb.st.count[b];
         for (int a = 0; a < bb.st.n_attrs; ++a)
-            bb.st.avg[a][b] = c ? __ddiv_rn(bb.st.sum[a][b], (double)c) : qnan;
+            bb.st.avg[a][b] = c ? bin_average(bb.st.sum[a][b], c) : qnan;
     }
 }
 
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(1024) k_batch_bin(const BatchBlock* blocks, co
         const int item = s_item;
         __syncthreads();
         if (item >= n_items) break;
-        const int4 it = items[item];  // {block, tile index, -, -}
+        const int4 it = items[item];  // {block, tile index, band, -}
         const BatchBlock& bb = blocks[it.x];
         const int64_t p0 = (int64_t)it.y * bb.tile;
         const int64_t p1 = min(bb.n, p0 + bb.tile);
@@ -105,7 +107,65 @@ __global__ void __launch_bounds__(1024) k_batch_bin(const BatchBlock* blocks, co
         const T* __restrict__ Y = static_cast<const T*>(bb.y);
         const T* acol[A_CT > 0 ? A_CT : kMaxAttr];
         for (int a = 0; a < A; ++a) acol[a] = static_cast<const T*>(bb.a[a]);
-        if (bb.strategy == BN_STRATEGY_PRIVATE) {
+        if (bb.strategy == BN_STRATEGY_PRIVATE && bb.bands > 1) {
+            // one band of the mesh (rows r0 .. r0 + nrows): every particle
+            // of the tile is located, those of other bands are skipped
+            // before their attributes are read
+            SmemMesh<T, MODE> m;
+            const int rx = bb.g.ax[0].res, ry = bb.g.ax[1].res;
+            const int r0 = it.z * bb.band_rows;
+            const int nrows = min(bb.band_rows, ry - r0);
+            const int B = nrows * rx, base = r0 * rx;
+            m.carve(smem, B, A, bb.st.do_sum != 0, bb.st.do_min != 0, bb.st.do_max != 0);
+            m.clear(A);
+            __syncthreads();
+            if (MODE == kSumLimbs && bb.st.do_sum) {
+                const int64_t i = p0 + threadIdx.x;
+                if (i < p1)
+                    for (int a = 0; a < A; ++a) m.sample(a, acol[a][i]);
+                m.bind_fallback(bb.st.sum, base);
+                __syncthreads();
+            }
+            const int64_t step = blockDim.x;
+            for (int64_t i0 = p0 + threadIdx.x; i0 < p1; i0 += 4 * step) {
+                T xs[4], ys[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t i = i0 + u * step;
+                    xs[u] = i < p1 ? __ldcs(X + i) : T(0);
+                    ys[u] = i < p1 ? __ldcs(Y + i) : T(0);
+                }
+                int l[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int b = i0 + u * step < p1 ? binner.bin(xs[u], ys[u]) : -1;
+                    l[u] = (b >= base && b < base + B) ? b - base : -1;
+                }
+                constexpr int AF = A_CT > 0 ? A_CT : 1;
+                T vs[4][AF];
+                if (A_CT > 0) {
+#pragma unroll
+                    for (int a = 0; a < AF; ++a)
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (l[u] >= 0) vs[u][a] = __ldcs(acol[a] + i0 + u * step);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (l[u] < 0) continue;
+                    m.add_count(l[u]);
+                    if (A_CT > 0) {
+#pragma unroll
+                        for (int a = 0; a < AF; ++a) m.add(a, l[u], vs[u][a]);
+                    } else {
+                        for (int a = 0; a < A; ++a) m.add(a, l[u], acol[a][i0 + u * step]);
+                    }
+                }
+            }
+            __syncthreads();
+            m.merge(bb.st, A, base, B);
+            __syncthreads();
+        } else if (bb.strategy == BN_STRATEGY_PRIVATE) {
             SmemMesh<T, MODE> m;
             const int B = bb.g.ax[0].res * bb.g.ax[1].res;
             m.carve(smem, B, A, bb.st.do_sum != 0, bb.st.do_min != 0, bb.st.do_max != 0);

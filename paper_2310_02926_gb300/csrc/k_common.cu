@@ -230,8 +230,8 @@ __global__ void k_grid_setup(GridDesc host_desc, const T* bounds_acc, GridDesc* 
 }
 
 // ------------------------------------------------------------------ finalise
-// avg = sum / count in FP64 (round-to-nearest division); empty bins get the
-// quiet NaN 0x7ff8000000000000.
+// avg = sum / count in FP64 (round-to-nearest, bin_average); empty bins get
+// the quiet NaN 0x7ff8000000000000.
 // With key state (st.mmk), also writes min and max from their keys.
 template <typename T>
 __global__ void k_finalize(StateDesc st) {
@@ -241,9 +241,8 @@ __global__ void k_finalize(StateDesc st) {
     using KO = KeyOf<T>;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += stride) {
         unsigned long long c = st.do_avg ? st.count[b] : 0ull;
-        double dc = (double)c;
         for (int a = 0; a < st.n_attrs; ++a) {
-            if (st.do_avg) st.avg[a][b] = c ? __ddiv_rn(st.sum[a][b], dc) : qnan;
+            if (st.do_avg) st.avg[a][b] = c ? bin_average(st.sum[a][b], c) : qnan;
             if (st.mmk) {
                 const int rp = key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
                 const auto k = static_cast<const typename KO::K2*>(st.mmk)[b * rp + a];

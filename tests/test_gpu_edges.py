@@ -200,3 +200,35 @@ def test_edges_static_entry(bn, dtype, grid):
                                           torch.cuda.current_stream().cuda_stream, 1)
     assert st == bn.OK, bn.lib().bn_last_error()
     check(w, to_numpy_result(out), tol_of(dtype), "static")
+
+
+def test_average_is_the_rounded_quotient(bn, ctx):
+    """avg = RN(sum / count) bit for bit (Sec. 4.2's per-bin average): counts
+    of 1, powers of two (exact scaling, including results in the subnormal
+    range) and other counts (FP64 division), over signed zeros, subnormal,
+    huge, inf and NaN sums. The expected value is numpy's IEEE division.
+    The exchange unpack finalises arbitrary counts and sums."""
+    rng = np.random.default_rng(81)
+    counts = np.array([1, 2, 3, 4, 5, 7, 8, 1024, 1023, 1 << 20, (1 << 20) + 1, 1 << 40, 3 << 30,
+                       6, 12, 96, 65536, 65537], dtype=np.int64)
+    specials = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2250738585072014e-308, 1e-310, 3e-320,
+                         1.7976931348623157e308, -1.7976931348623157e308, np.inf, -np.inf, np.nan,
+                         1.0, -1.0, 0.1, 1.0 / 3.0, 6.0, -96.0])
+    randoms = rng.standard_normal(2000) * 10.0 ** rng.integers(-300, 300, 2000)
+    sums = np.concatenate([specials, randoms])
+    S, C = np.meshgrid(sums, counts, indexing="ij")
+    S, C = S.ravel(), C.ravel()
+    B, A = S.size, 1
+    ex = torch.zeros(bn.bn_exchange_bytes(B, A), dtype=torch.uint8, device="cuda")
+    sec = bn.exchange_sections(ex, B, A)
+    sec[0].copy_(torch.from_numpy(C))
+    sec[1].copy_(torch.from_numpy(S))
+    out = bn.alloc_outputs(A, B, torch.float64, torch.device("cuda"))
+    bn.bn_exchange_unpack(ctx.handle, ex, bn.F64, A, B, bn.OP_ALL, bn.result_struct(out))
+    torch.cuda.synchronize()
+    got = out["avg"][0].cpu().numpy()
+    with np.errstate(all="ignore"):
+        want = S / C.astype(np.float64)
+    nan = np.isnan(want)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan].view(np.int64), want[~nan].view(np.int64))

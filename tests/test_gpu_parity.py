@@ -543,6 +543,22 @@ def test_batch_persistent_path(bn, ctx, dtype, strategy):
             check(w, to_numpy_result(o), tol, label=f"{w.name} rep{rep}")
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_batch_private_in_mesh_bands(bn, ctx, dtype):
+    """Private strategy forced on meshes larger than shared memory: each mesh
+    is cut into bands of rows and every band of every tile is a work item of
+    its own; every block against the oracle, then the same shapes again with
+    new values (a replay of the cached graph)."""
+    plan = workloads.batch(n_blocks=10, seed=43, size_range=(1e4, 4e5), side_range=(80, 220))
+    tol = TOL_F64 if dtype == np.float64 else TOL_F32C
+    for rep, scale in enumerate((None, 7.0)):
+        blocks, outs, keep = _batch_blocks(bn, plan, dtype, scale=scale)
+        bn.bn_bin_batch(ctx.handle, blocks, bn.OP_ALL | bn.STRATEGY_PRIVATE)
+        torch.cuda.synchronize()
+        for w, o in outs:
+            check(w, to_numpy_result(o), tol, label=f"{w.name} rep{rep}")
+
+
 def test_batch_general_path_with_host_columns(bn, ctx):
     plan = workloads.batch(n_blocks=5, seed=42, size_range=(1e3, 5e4), side_range=(8, 200))
     blocks, outs, keep = _batch_blocks(bn, plan, np.float32, host=True)
