@@ -76,8 +76,19 @@ struct BatchGraph {
     size_t sort_args_off = 0;
     std::vector<size_t> sort_off;
     std::vector<SortDesc> sort_sd;
+    // side streams of the capture: the sort blocks' kernel chains are
+    // independent, so they fork off the context stream after the prepare
+    // launch and join it before the finalise (parallel graph branches)
+    static constexpr int kSide = 4;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr, join[kSide] = {};
     ~BatchGraph() {
         if (last) cudaEventSynchronize(last), cudaEventDestroy(last);
+        for (int s = 0; s < kSide; ++s) {
+            if (side[s]) cudaStreamDestroy(side[s]);
+            if (join[s]) cudaEventDestroy(join[s]);
+        }
+        if (fork) cudaEventDestroy(fork);
         if (exec) cudaGraphExecDestroy(exec);
         if (dev) cudaFree(dev);
         if (host) cudaFreeHost(host);
@@ -89,6 +100,7 @@ struct BatchGraph {
 struct BatchCache {
     std::mutex mu;
     std::map<ClassKey, Choice> choices;
+    std::map<std::vector<int64_t>, int> lean;  // batch shape -> sort-leaning plan chosen
     std::vector<std::unique_ptr<BatchGraph>> graphs;  // most recent last
 };
 
@@ -355,6 +367,185 @@ static float trial(bn_context* c, FastBlock f, int strategy, int aggregate, int 
     return ms;
 }
 
+// Find or build (capture once) the graph of the plan `fbs` describes and
+// launch it on the context stream.
+// The key of a plan's cached graph: everything that fixes its kernels and
+// launch shapes.
+static std::vector<int64_t> plan_shape(const std::vector<FastBlock>& fbs, int dtype, int A, uint32_t ops) {
+    std::vector<int64_t> shape;
+    shape.reserve(4 + 6 * fbs.size());
+    shape.push_back(dtype);
+    shape.push_back(A);
+    shape.push_back(ops & ~(uint32_t)BN_STRATEGY_MASK);
+    shape.push_back((int64_t)fbs.size());
+    for (const FastBlock& f : fbs) {
+        shape.push_back(f.bb.n);
+        shape.push_back(f.bb.g.ax[0].res);
+        shape.push_back(f.bb.g.ax[1].res);
+        shape.push_back(f.bb.strategy * 2 + f.bb.aggregate);
+        shape.push_back(f.bb.tile);
+        shape.push_back(f.bb.bands);
+    }
+    return shape;
+}
+
+static bn_status launch_plan(bn_context* c, BatchCache& cache, std::vector<FastBlock>& fbs, int dtype, int A,
+                             uint32_t ops, int sum_mode, bool want_avg, size_t smem) {
+    const int n_blocks = (int)fbs.size();
+    const std::vector<int64_t> shape = plan_shape(fbs, dtype, A, ops);
+    const int n_items = count_items(fbs);
+    int64_t total_edges = 0;
+    for (const FastBlock& f : fbs) total_edges += f.edges;
+    PlanLayout L = layout_for(n_blocks, n_items, total_edges);
+
+    BatchGraph* G = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(cache.mu);
+        for (auto& g : cache.graphs)
+            if (g->shape == shape) G = g.get();
+    }
+    int ni = n_items;
+    int64_t bins = 0, edges = 0;
+    for (const FastBlock& f : fbs) bins += f.bins;
+    edges = total_edges;
+    if (!G) {
+        std::unique_ptr<BatchGraph> ng(new BatchGraph());
+        ng->shape = shape;
+        cudaError_t e = cudaMalloc(&ng->dev, L.bytes);
+        if (e == cudaSuccess) e = cudaHostAlloc(&ng->host, L.bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ng->last, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: plan memory");
+        fill_plan(fbs, L, static_cast<unsigned char*>(ng->host), static_cast<unsigned char*>(ng->dev), &ni,
+                  &bins, &edges, dtype);
+        ng->h_blocks = reinterpret_cast<BatchBlock*>(static_cast<unsigned char*>(ng->host) + L.off_blocks);
+        ng->d_blocks = reinterpret_cast<BatchBlock*>(static_cast<unsigned char*>(ng->dev) + L.off_blocks);
+        // the static part (starts, items) goes over once
+        e = cudaMemcpy(ng->dev, ng->host, L.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: plan upload");
+        std::lock_guard<std::mutex> lk(cache.mu);
+        cache.graphs.push_back(std::move(ng));
+        if (cache.graphs.size() > 8) cache.graphs.erase(cache.graphs.begin());
+        G = cache.graphs.back().get();
+    } else {
+        // same shape: wait until the pinned descriptors are free, rewrite them
+        cudaEventSynchronize(G->last);
+        unsigned char* host = static_cast<unsigned char*>(G->host);
+        int64_t edge_off = 0;
+        for (int k = 0; k < n_blocks; ++k) {
+            FastBlock& f = fbs[k];
+            if (dtype == BN_F64) {
+                long long* d_edges = reinterpret_cast<long long*>(static_cast<unsigned char*>(G->dev) + L.off_edges);
+                f.bb.g.edges[0] = d_edges + edge_off;
+                f.bb.g.edges[1] = d_edges + edge_off + f.bb.g.ax[0].res + 1;
+                edge_off += f.edges;
+            }
+            reinterpret_cast<BatchBlock*>(host + L.off_blocks)[k] = f.bb;
+        }
+    }
+
+    // blocks on the sort path: scratch and argument copies in the plan's own
+    // memory (sized once per plan shape), arguments rewritten every call
+    std::vector<const FastBlock*> sort_blocks;
+    for (const FastBlock& f : fbs)
+        if (f.bb.strategy == BN_STRATEGY_SORT && f.bb.n > 0) sort_blocks.push_back(&f);
+    const size_t n_sorts = sort_blocks.size();
+    if (n_sorts && !G->sort_dev) {
+        size_t off = 0;
+        for (const FastBlock* f : sort_blocks) {
+            const BinArgs a = sort_args(*f, dtype, A, sum_mode);
+            SortDesc sd;
+            if (!sort_plan(a, c->smem_optin, &sd)) return fail(BN_ERR_INTERNAL, "bn_bin_batch: no sort plan");
+            G->sort_sd.push_back(sd);
+            G->sort_off.push_back(off);
+            off += align256(sort_scratch_bytes(sd, a));
+        }
+        G->sort_args_off = off;
+        off += align256(sizeof(BinArgs) * n_sorts);
+        cudaError_t e = cudaMalloc(&G->sort_dev, off);
+        if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&G->sort_args), sizeof(BinArgs) * n_sorts,
+                                                cudaHostAllocDefault);
+        if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: sort plan memory");
+    }
+    // the previous replay has released the pinned copies (G->last waited above)
+    for (size_t j = 0; j < n_sorts; ++j) G->sort_args[j] = sort_args(*sort_blocks[j], dtype, A, sum_mode);
+    unsigned char* sdev = static_cast<unsigned char*>(G->sort_dev);
+    BinArgs* d_sort_args = n_sorts ? reinterpret_cast<BinArgs*>(sdev + G->sort_args_off) : nullptr;
+
+    unsigned char* d = static_cast<unsigned char*>(G->dev);
+    std::atomic<uint64_t> nlaunch{0};
+    const KernelCtx kc{c->stream, c->num_sms, c->smem_optin, &nlaunch};
+    // parallel: fork the sort blocks' chains onto the side streams (capture
+    // only; a direct launch keeps them on the context stream, in order)
+    auto body = [&](bool parallel) {
+        cudaError_t e2 = cudaMemcpyAsync(G->d_blocks, G->h_blocks, sizeof(BatchBlock) * n_blocks,
+                                         cudaMemcpyHostToDevice, c->stream);
+        if (e2 == cudaSuccess) e2 = cudaMemsetAsync(d + L.off_counter, 0, sizeof(int), c->stream);
+        if (e2 == cudaSuccess)
+            e2 = launch_batch_prepare(kc, dtype, G->d_blocks, reinterpret_cast<int64_t*>(d + L.off_bin_start),
+                                      reinterpret_cast<int64_t*>(d + L.off_edge_start), n_blocks, bins, edges);
+        if (e2 == cudaSuccess && n_sorts)
+            e2 = cudaMemcpyAsync(d_sort_args, G->sort_args, sizeof(BinArgs) * n_sorts, cudaMemcpyHostToDevice,
+                                 c->stream);
+        const int n_side = parallel ? (int)std::min<size_t>(n_sorts, BatchGraph::kSide) : 0;
+        if (e2 == cudaSuccess && n_side > 0) {
+            e2 = cudaEventRecord(G->fork, c->stream);
+            for (int k = 0; k < n_side && e2 == cudaSuccess; ++k) e2 = cudaStreamWaitEvent(G->side[k], G->fork, 0);
+        }
+        for (size_t j = 0; j < n_sorts && e2 == cudaSuccess; ++j) {
+            KernelCtx kj = kc;
+            if (n_side > 0) kj.stream = G->side[j % n_side];
+            e2 = launch_bin_sort(kj, G->sort_args[j], G->sort_sd[j], sdev + G->sort_off[j], d_sort_args + j);
+        }
+        if (e2 == cudaSuccess && ni > 0)
+            e2 = launch_batch_bin(kc, dtype, sum_mode, G->d_blocks, reinterpret_cast<int4*>(d + L.off_items), ni,
+                                  reinterpret_cast<int*>(d + L.off_counter), A, smem);
+        for (int k = 0; k < n_side && e2 == cudaSuccess; ++k) {
+            e2 = cudaEventRecord(G->join[k], G->side[k]);
+            if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(c->stream, G->join[k], 0);
+        }
+        if (e2 == cudaSuccess && want_avg)
+            e2 = launch_batch_finalize(kc, G->d_blocks, reinterpret_cast<int64_t*>(d + L.off_bin_start), n_blocks, bins);
+        return e2;
+    };
+    const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy;
+    if (!capturable) {
+        // no graph on the legacy stream: launch directly
+        cudaError_t e2 = body(false);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "bn_bin_batch: launch");
+        c->launches.fetch_add(nlaunch.load());
+        cudaEventRecord(G->last, c->stream);
+        return BN_OK;
+    }
+    if (!G->exec) {
+        // capture once per plan shape: every per-call value (block
+        // descriptors, sort arguments) reaches the kernels through the plan's
+        // memory, which the graph's copy nodes rewrite from pinned buffers
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaSuccess;
+        if (n_sorts && !G->fork) {
+            e = cudaEventCreateWithFlags(&G->fork, cudaEventDisableTiming);
+            for (int k = 0; k < BatchGraph::kSide && e == cudaSuccess; ++k) {
+                e = cudaStreamCreateWithFlags(&G->side[k], cudaStreamNonBlocking);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->join[k], cudaEventDisableTiming);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: side streams");
+        }
+        e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        cudaError_t eb = e == cudaSuccess ? body(n_sorts > 0) : e;
+        cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+        if (e == cudaSuccess) e = eb != cudaSuccess ? eb : ee;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&G->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: graph capture");
+        G->launches = nlaunch.load();
+    }
+    cudaError_t e = cudaGraphLaunch(G->exec, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: graph launch");
+    c->launches.fetch_add(G->launches);
+    cudaEventRecord(G->last, c->stream);
+    return BN_OK;
+}
+
 // Mesh bands for a private block whose whole mesh exceeds shared memory:
 // the fewest bands of whole rows that fit, rows spread evenly over them
 // (bands = 0: not even one row fits, or more than kMaxBands are needed).
@@ -529,148 +720,89 @@ static bn_status batch_fast(bn_context* c, const bn_block* blocks, int n_blocks,
         if (ch.strategy == BN_STRATEGY_PRIVATE) smem = std::max(smem, banded ? bl.bytes : mesh);
     }
 
-    // ---- plan shape and graph
-    std::vector<int64_t> shape;
-    shape.reserve(4 + 5 * (size_t)n_blocks);
-    shape.push_back(dtype);
-    shape.push_back(A);
-    shape.push_back(ops & ~(uint32_t)BN_STRATEGY_MASK);
-    shape.push_back(n_blocks);
-    for (const FastBlock& f : fbs) {
-        shape.push_back(f.bb.n);
-        shape.push_back(f.bb.g.ax[0].res);
-        shape.push_back(f.bb.g.ax[1].res);
-        shape.push_back(f.bb.strategy * 2 + f.bb.aggregate);
-        shape.push_back(f.bb.tile);
-        shape.push_back(f.bb.bands);
-    }
-    const int n_items = count_items(fbs);
-    int64_t total_edges = 0;
-    for (const FastBlock& f : fbs) total_edges += f.edges;
-    PlanLayout L = layout_for(n_blocks, n_items, total_edges);
-
-    BatchGraph* G = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(cache.mu);
-        for (auto& g : cache.graphs)
-            if (g->shape == shape) G = g.get();
-    }
-    int ni = n_items;
-    int64_t bins = 0, edges = 0;
-    for (const FastBlock& f : fbs) bins += f.bins;
-    edges = total_edges;
-    if (!G) {
-        std::unique_ptr<BatchGraph> ng(new BatchGraph());
-        ng->shape = shape;
-        cudaError_t e = cudaMalloc(&ng->dev, L.bytes);
-        if (e == cudaSuccess) e = cudaHostAlloc(&ng->host, L.bytes, cudaHostAllocDefault);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ng->last, cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: plan memory");
-        fill_plan(fbs, L, static_cast<unsigned char*>(ng->host), static_cast<unsigned char*>(ng->dev), &ni,
-                  &bins, &edges, dtype);
-        ng->h_blocks = reinterpret_cast<BatchBlock*>(static_cast<unsigned char*>(ng->host) + L.off_blocks);
-        ng->d_blocks = reinterpret_cast<BatchBlock*>(static_cast<unsigned char*>(ng->dev) + L.off_blocks);
-        // the static part (starts, items) goes over once
-        e = cudaMemcpy(ng->dev, ng->host, L.bytes, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: plan upload");
-        std::lock_guard<std::mutex> lk(cache.mu);
-        cache.graphs.push_back(std::move(ng));
-        if (cache.graphs.size() > 8) cache.graphs.erase(cache.graphs.begin());
-        G = cache.graphs.back().get();
-    } else {
-        // same shape: wait until the pinned descriptors are free, rewrite them
-        cudaEventSynchronize(G->last);
-        unsigned char* host = static_cast<unsigned char*>(G->host);
-        int64_t edge_off = 0;
-        for (int k = 0; k < n_blocks; ++k) {
-            FastBlock& f = fbs[k];
-            if (dtype == BN_F64) {
-                long long* d_edges = reinterpret_cast<long long*>(static_cast<unsigned char*>(G->dev) + L.off_edges);
-                f.bb.g.edges[0] = d_edges + edge_off;
-                f.bb.g.edges[1] = d_edges + edge_off + f.bb.g.ax[0].res + 1;
-                edge_off += f.edges;
+    // ---- batch-level check of the per-class choices: inside a batch the sort
+    // blocks' kernel chains run as parallel graph branches, which a block's
+    // trial alone cannot show, so the first call on a batch shape also times
+    // the whole batch with every block of at least 2^16 particles on the sort
+    // path, and keeps the faster plan for that shape
+    if (!forced && n_blocks > 1) {
+        std::vector<int64_t> key{dtype, A, (int64_t)(ops & ~(uint32_t)BN_STRATEGY_MASK), n_blocks};
+        for (const FastBlock& f : fbs) {
+            key.push_back(f.bb.n);
+            key.push_back(f.bb.g.ax[0].res);
+            key.push_back(f.bb.g.ax[1].res);
+        }
+        std::vector<FastBlock> lean = fbs;
+        size_t lean_smem = 0;
+        bool differs = false;
+        for (FastBlock& f : lean) {
+            SortDesc probe;
+            if (f.bb.strategy != BN_STRATEGY_SORT && f.bb.n >= (1 << 16) &&
+                sort_plan(sort_args(f, dtype, A, sum_mode), c->smem_optin, &probe)) {
+                f.bb.strategy = BN_STRATEGY_SORT;
+                f.bb.aggregate = 0;
+                f.bb.bands = 1;
+                f.bb.band_rows = f.bb.g.ax[1].res;
+                f.bb.tile = choose_tile(BN_STRATEGY_SORT, f.bb.n, f.bins, c->num_sms);
+                differs = true;
+            } else if (f.bb.strategy == BN_STRATEGY_PRIVATE) {
+                lean_smem = std::max(lean_smem, private_mesh_bytes(dtype, sum_mode,
+                                                                   (int64_t)f.bb.band_rows * f.bb.g.ax[0].res, A,
+                                                                   f.bb.st.do_sum, want_min, want_max));
             }
-            reinterpret_cast<BatchBlock*>(host + L.off_blocks)[k] = f.bb;
+        }
+        int use_lean = -1;
+        {
+            std::lock_guard<std::mutex> lk(cache.mu);
+            auto it = cache.lean.find(key);
+            if (it != cache.lean.end()) use_lean = it->second;
+        }
+        if (differs && use_lean < 0) {
+            float t[2] = {-1.0f, -1.0f};
+            for (int v = 0; v < 2; ++v) {
+                std::vector<FastBlock>& fv = v ? lean : fbs;
+                const size_t sm = v ? lean_smem : smem;
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                bn_status st = BN_OK;
+                if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+                    for (int rep = 0; rep < 2 && st == BN_OK; ++rep)  // builds, then warms the plan
+                        st = launch_plan(c, cache, fv, dtype, A, ops, sum_mode, want_avg, sm);
+                    if (st == BN_OK) cudaEventRecord(e0, c->stream);
+                    if (st == BN_OK) st = launch_plan(c, cache, fv, dtype, A, ops, sum_mode, want_avg, sm);
+                    if (st == BN_OK && cudaEventRecord(e1, c->stream) == cudaSuccess &&
+                        cudaEventSynchronize(e1) == cudaSuccess)
+                        cudaEventElapsedTime(&t[v], e0, e1);
+                }
+                if (e0) cudaEventDestroy(e0);
+                if (e1) cudaEventDestroy(e1);
+                if (st != BN_OK) return st;
+            }
+            use_lean = (t[1] >= 0.0f && t[1] < t[0]) ? 1 : 0;
+            {
+                // drop the slower plan's graph and memory (its last replay
+                // has finished: the timed launch was waited for)
+                const std::vector<int64_t> lose = plan_shape(use_lean ? fbs : lean, dtype, A, ops);
+                std::lock_guard<std::mutex> lk(cache.mu);
+                cache.lean[key] = use_lean;
+                for (size_t g = 0; g < cache.graphs.size(); ++g)
+                    if (cache.graphs[g]->shape == lose) {
+                        cache.graphs.erase(cache.graphs.begin() + (long)g);
+                        break;
+                    }
+            }
+            char msg[160];
+            snprintf(msg, sizeof msg, "batch of %d blocks: per-class plan=%.3fms sort-leaning plan=%.3fms -> %s",
+                     n_blocks, t[0], t[1], use_lean ? "sort-leaning" : "per-class");
+            std::lock_guard<std::mutex> lk2(c->tune_mu);
+            c->tune_log.push_back(msg);
+        }
+        if (differs && use_lean == 1) {
+            fbs.swap(lean);
+            smem = lean_smem;
         }
     }
-
-    // blocks on the sort path: scratch and argument copies in the plan's own
-    // memory (sized once per plan shape), arguments rewritten every call
-    std::vector<const FastBlock*> sort_blocks;
-    for (const FastBlock& f : fbs)
-        if (f.bb.strategy == BN_STRATEGY_SORT && f.bb.n > 0) sort_blocks.push_back(&f);
-    const size_t n_sorts = sort_blocks.size();
-    if (n_sorts && !G->sort_dev) {
-        size_t off = 0;
-        for (const FastBlock* f : sort_blocks) {
-            const BinArgs a = sort_args(*f, dtype, A, sum_mode);
-            SortDesc sd;
-            if (!sort_plan(a, c->smem_optin, &sd)) return fail(BN_ERR_INTERNAL, "bn_bin_batch: no sort plan");
-            G->sort_sd.push_back(sd);
-            G->sort_off.push_back(off);
-            off += align256(sort_scratch_bytes(sd, a));
-        }
-        G->sort_args_off = off;
-        off += align256(sizeof(BinArgs) * n_sorts);
-        cudaError_t e = cudaMalloc(&G->sort_dev, off);
-        if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&G->sort_args), sizeof(BinArgs) * n_sorts,
-                                                cudaHostAllocDefault);
-        if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: sort plan memory");
-    }
-    // the previous replay has released the pinned copies (G->last waited above)
-    for (size_t j = 0; j < n_sorts; ++j) G->sort_args[j] = sort_args(*sort_blocks[j], dtype, A, sum_mode);
-    unsigned char* sdev = static_cast<unsigned char*>(G->sort_dev);
-    BinArgs* d_sort_args = n_sorts ? reinterpret_cast<BinArgs*>(sdev + G->sort_args_off) : nullptr;
-
-    unsigned char* d = static_cast<unsigned char*>(G->dev);
-    std::atomic<uint64_t> nlaunch{0};
-    const KernelCtx kc{c->stream, c->num_sms, c->smem_optin, &nlaunch};
-    auto body = [&]() {
-        cudaError_t e2 = cudaMemcpyAsync(G->d_blocks, G->h_blocks, sizeof(BatchBlock) * n_blocks,
-                                         cudaMemcpyHostToDevice, c->stream);
-        if (e2 == cudaSuccess)
-            e2 = queue_batch(kc, dtype, sum_mode, A, G->d_blocks, reinterpret_cast<int64_t*>(d + L.off_bin_start),
-                             reinterpret_cast<int64_t*>(d + L.off_edge_start),
-                             reinterpret_cast<int4*>(d + L.off_items), reinterpret_cast<int*>(d + L.off_counter),
-                             n_blocks, ni, bins, edges, smem, false);
-        if (e2 == cudaSuccess && n_sorts)
-            e2 = cudaMemcpyAsync(d_sort_args, G->sort_args, sizeof(BinArgs) * n_sorts, cudaMemcpyHostToDevice,
-                                 c->stream);
-        for (size_t j = 0; j < n_sorts && e2 == cudaSuccess; ++j)
-            e2 = launch_bin_sort(kc, G->sort_args[j], G->sort_sd[j], sdev + G->sort_off[j], d_sort_args + j);
-        if (e2 == cudaSuccess && want_avg)
-            e2 = launch_batch_finalize(kc, G->d_blocks, reinterpret_cast<int64_t*>(d + L.off_bin_start), n_blocks, bins);
-        return e2;
-    };
-    const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy;
-    if (!capturable) {
-        // no graph on the legacy stream: launch directly
-        cudaError_t e2 = body();
-        if (e2 != cudaSuccess) return cuda_fail(e2, "bn_bin_batch: launch");
-        c->launches.fetch_add(nlaunch.load());
-        cudaEventRecord(G->last, c->stream);
-        return BN_OK;
-    }
-    if (!G->exec) {
-        // capture once per plan shape: every per-call value (block
-        // descriptors, sort arguments) reaches the kernels through the plan's
-        // memory, which the graph's copy nodes rewrite from pinned buffers
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-        cudaError_t eb = e == cudaSuccess ? body() : e;
-        cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
-        if (e == cudaSuccess) e = eb != cudaSuccess ? eb : ee;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&G->exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: graph capture");
-        G->launches = nlaunch.load();
-    }
-    cudaError_t e = cudaGraphLaunch(G->exec, c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "bn_bin_batch: graph launch");
-    c->launches.fetch_add(G->launches);
-    cudaEventRecord(G->last, c->stream);
     (void)r;
-    return BN_OK;
+    return launch_plan(c, cache, fbs, dtype, A, ops, sum_mode, want_avg, smem);
 }
 
 extern "C" bn_status bn_bin_batch(bn_context* c, const bn_block* blocks, int n_blocks,
