@@ -30,6 +30,7 @@
 
 #include <climits>
 #include <cstring>
+#include <type_traits>
 
 #include "bn_device.cuh"
 #include "bn_internal.cuh"
@@ -157,8 +158,37 @@ __global__ void k_sort_plan(SortDesc sd) {
 // each bucket is reserved, and then the attributes are loaded and written
 // straight to their sorted slot in shared memory, so registers hold only
 // (bucket, local bin, rank) per particle. The sorted records then go out to
-// their reserved runs.
-template <typename T, int A_CT, int PER>
+// their reserved runs. VEC (every column 16-byte aligned): a thread's
+// particles come in 16-byte vectors, vector v of the tile holding particles
+// v*VN .. v*VN+VN-1; otherwise one coalesced element per load.
+template <typename T>
+__device__ __forceinline__ void load_group8(const T* __restrict__ col, int64_t base, int j0, int64_t n,
+                                            bool vec, T* out) {
+    constexpr int VN = VecOf<T>::N;
+    using V = typename VecOf<T>::type;
+    if (vec) {
+#pragma unroll
+        for (int q = 0; q < 8 / VN; ++q) {
+            const int64_t p0 = base + ((int64_t)(j0 / VN + q) * blockDim.x + threadIdx.x) * VN;
+            if (p0 + VN <= n) {
+                const V v = __ldcs(reinterpret_cast<const V*>(col + p0));
+#pragma unroll
+                for (int e = 0; e < VN; ++e) out[q * VN + e] = vget<T>(v, e);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VN; ++e) out[q * VN + e] = p0 + e < n ? __ldcs(col + p0 + e) : T(0);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t p = base + (int64_t)(j0 + u) * blockDim.x + threadIdx.x;
+            out[u] = p < n ? __ldcs(col + p) : T(0);
+        }
+    }
+}
+
+template <typename T, int A_CT, int PER, bool VEC>
 __global__ void __launch_bounds__(1024) k_sort_scatter(BinArgs args_v, SortDesc sd, const BinArgs* dargs) {
     const BinArgs& args = dargs ? *dargs : args_v;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -185,6 +215,12 @@ __global__ void __launch_bounds__(1024) k_sort_scatter(BinArgs args_v, SortDesc 
 
     const T* __restrict__ X = static_cast<const T*>(args.x);
     const T* __restrict__ Y = static_cast<const T*>(args.y);
+    constexpr int VN = VecOf<T>::N;
+    // the particle that is this thread's j-th
+    auto pidx = [&](int j) -> int64_t {
+        return VEC ? base + ((int64_t)(j / VN) * blockDim.x + threadIdx.x) * VN + (j % VN)
+                   : base + (int64_t)j * blockDim.x + threadIdx.x;
+    };
     int bucket[PER], slot[PER];  // slot = local bin | rank << 16, then the sorted position
     {
         // coordinates in groups of 8 per thread, so only the bucket and slot
@@ -192,16 +228,12 @@ __global__ void __launch_bounds__(1024) k_sort_scatter(BinArgs args_v, SortDesc 
 #pragma unroll
         for (int j0 = 0; j0 < PER; j0 += 8) {
             T xv[8], yv[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int64_t p = base + (j0 + u) * blockDim.x + threadIdx.x;
-                xv[u] = p < n ? __ldcs(X + p) : T(0);
-                yv[u] = p < n ? __ldcs(Y + p) : T(0);
-            }
+            load_group8<T>(X, base, j0, n, VEC, xv);
+            load_group8<T>(Y, base, j0, n, VEC, yv);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int j = j0 + u;
-                const int64_t p = base + j * blockDim.x + threadIdx.x;
+                const int64_t p = pidx(j);
                 const int b = p < n ? binner.bin(xv[u], yv[u]) : -1;
                 bucket[j] = b < 0 ? -1 : (b >> sd.log2bk);
                 // rank within the tile's bucket: the value the shared atomic
@@ -260,11 +292,7 @@ __global__ void __launch_bounds__(1024) k_sort_scatter(BinArgs args_v, SortDesc 
 #pragma unroll
         for (int j0 = 0; j0 < PER; j0 += 8) {
             T v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int64_t p = base + (j0 + u) * blockDim.x + threadIdx.x;
-                v[u] = slot[j0 + u] >= 0 ? __ldcs(col + p) : T(0);
-            }
+            load_group8<T>(col, base, j0, n, VEC, v);
 #pragma unroll
             for (int u = 0; u < 8; ++u)
                 if (slot[j0 + u] >= 0) sattr[a * TP + slot[j0 + u]] = v[u];
@@ -319,21 +347,74 @@ __global__ void __launch_bounds__(1024) k_sort_reduce(BinArgs args_v, SortDesc s
                 for (int a = 0; a < A; ++a) m.sample(a, attrs[(int64_t)a * S + r]);
             __syncthreads();
         }
-        for (int r0 = it.y + threadIdx.x; r0 < it.z; r0 += U * blockDim.x) {
-            int l[U];
-            T v[U][AC];
+        if constexpr (A_CT >= 0 && A_CT <= 4) {
+            // 16-byte loads: groups of VN records (the record planes start
+            // on 16-byte boundaries, S being a multiple of 32); the records
+            // before the first and after the last whole group one by one
+            constexpr int VN = VecOf<T>::N;
+            constexpr int G = 2;  // groups per thread per step, loads first
+            using V = typename VecOf<T>::type;
+            using KV = typename std::conditional<VN == 4, uint2, unsigned>::type;
+            const int y = it.y, z = it.z;
+            const int vb = min(z, (y + VN - 1) / VN * VN);
+            const int ve = max(vb, z / VN * VN);
+            auto one = [&](int r) {
+                const int l = (int)__ldcs(keys + r);
+                m.add_count(l);
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int r = r0 + u * blockDim.x;
-                l[u] = r < it.z ? (int)__ldcs(keys + r) : -1;
-                if (l[u] >= 0)
-                    for (int a = 0; a < A; ++a) v[u][a] = __ldcs(attrs + (int64_t)a * S + r);
+                for (int a = 0; a < A_CT; ++a) m.add(a, l, __ldcs(attrs + (int64_t)a * S + r));
+            };
+            for (int r = y + (int)threadIdx.x; r < vb; r += blockDim.x) one(r);
+            for (int r = ve + (int)threadIdx.x; r < z; r += blockDim.x) one(r);
+            const int ng = (ve - vb) / VN;
+            const KV* KG = reinterpret_cast<const KV*>(keys + vb);
+            const V* AG[AC];
+#pragma unroll
+            for (int a = 0; a < AC; ++a) AG[a] = reinterpret_cast<const V*>(attrs + (int64_t)(a < A_CT ? a : 0) * S + vb);
+            for (int g0 = threadIdx.x; g0 < ng; g0 += G * blockDim.x) {
+                KV kk[G];
+                V av[G][AC];
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    const int g = g0 + k * blockDim.x;
+                    if (g < ng) {
+                        kk[k] = __ldcs(KG + g);
+#pragma unroll
+                        for (int a = 0; a < A_CT; ++a) av[k][a] = __ldcs(AG[a] + g);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    if (g0 + k * (int)blockDim.x >= ng) break;
+#pragma unroll
+                    for (int j = 0; j < VN; ++j) {
+                        unsigned w;
+                        if constexpr (VN == 4) w = (j < 2) ? kk[k].x : kk[k].y;
+                        else w = kk[k];
+                        const int l = (int)((w >> (16 * (j & 1))) & 0xffffu);
+                        m.add_count(l);
+#pragma unroll
+                        for (int a = 0; a < A_CT; ++a) m.add(a, l, vget<T>(av[k][a], j));
+                    }
+                }
             }
+        } else {
+            for (int r0 = it.y + threadIdx.x; r0 < it.z; r0 += U * blockDim.x) {
+                int l[U];
+                T v[U][AC];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (l[u] < 0) continue;
-                m.add_count(l[u]);
-                for (int a = 0; a < A; ++a) m.add(a, l[u], v[u][a]);
+                for (int u = 0; u < U; ++u) {
+                    const int r = r0 + u * blockDim.x;
+                    l[u] = r < it.z ? (int)__ldcs(keys + r) : -1;
+                    if (l[u] >= 0)
+                        for (int a = 0; a < A; ++a) v[u][a] = __ldcs(attrs + (int64_t)a * S + r);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (l[u] < 0) continue;
+                    m.add_count(l[u]);
+                    for (int a = 0; a < A; ++a) m.add(a, l[u], v[u][a]);
+                }
             }
         }
         __syncthreads();
@@ -392,7 +473,9 @@ bool sort_plan(const BinArgs& a, int smem_optin_total, SortDesc* sd) {
     sd->tp = tp;
     sd->per = tp >= 8192 ? 16 : 8;  // 1024, 512, 512, 256 threads
     sd->tiles = (a.n + tp - 1) / tp;
-    sd->slots = a.n > 0 ? a.n : 1;
+    // record capacity, a multiple of 32 so that every attribute plane starts
+    // on a 16-byte boundary (the reduce pass reads records in 16-byte groups)
+    sd->slots = ((a.n > 0 ? a.n : 1) + 31) & ~(int64_t)31;
     sd->chunk = kLimbMaxAdds;  // records per work item; also bounds a limb mesh's adds per bin
     sd->off_gpos = (int)align256((size_t)(nb + 1) * 4);
     sd->off_skey = sd->off_gpos + (int)align256((size_t)nb * 4);
@@ -420,7 +503,14 @@ size_t sort_scratch_bytes(const SortDesc& sd, const BinArgs& a) {
 template <typename T, int A_CT, int MODE>
 static cudaError_t launch_sort_t(const KernelCtx& kc, const BinArgs& a, const SortDesc& sd,
                                  const BinArgs* dargs) {
-    auto scat = sd.per == 16 ? k_sort_scatter<T, A_CT, 16> : k_sort_scatter<T, A_CT, 8>;
+    // 16-byte column loads when every column allows them
+    bool vec = true;
+    for (int k = -2; k < a.n_attrs; ++k) {
+        const void* p = k == -2 ? a.x : k == -1 ? a.y : a.a[k];
+        vec = vec && ((uintptr_t)p % 16) == 0;
+    }
+    auto scat = vec ? (sd.per == 16 ? k_sort_scatter<T, A_CT, 16, true> : k_sort_scatter<T, A_CT, 8, true>)
+                    : (sd.per == 16 ? k_sort_scatter<T, A_CT, 16, false> : k_sort_scatter<T, A_CT, 8, false>);
     auto red = k_sort_reduce<T, A_CT, MODE>;
     auto cnt = k_sort_count<T>;
     // the opt-in limit covers static plus dynamic shared memory
