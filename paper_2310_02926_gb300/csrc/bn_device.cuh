@@ -626,6 +626,37 @@ struct FltPairs {
 //  - key records alone (st.mmk): the record is read, an atomic is issued
 //    only where the key would change it;
 //  - the outputs themselves (raw IEEE bits, totalOrder atomics).
+// The f64 filter form of commit_minmax once bin b's filter record f has been
+// read (load_filter): only keys whose top half reaches the filter's bound
+// update the key record, then lower (raise) the filter.
+template <int A_CT>
+__device__ __forceinline__ void apply_filtered_minmax(const StateDesc& st, int A, int64_t b, const double* lo,
+                                                      const double* hi, const int2* f) {
+    using KO = KeyOf<double>;
+    using K2 = typename KO::K2;
+    int2* fr = static_cast<int2*>(st.mmf) + b * filter_record_pairs(st.n_attrs);
+    K2* kr = static_cast<K2*>(st.mmk) + b * key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
+    for (int a = 0; a < A; ++a) {
+        const long long kl = KO::key(lo[a]), kh = KO::key(hi[a]);
+        const int hl = (int)(kl >> 32), hh = (int)(kh >> 32);  // order preserving
+        if (st.do_min && hl <= f[a].x && !is_nan_bits(lo[a])) {
+            atomicMin(&kr[a].x, kl);
+            if (hl < f[a].x) atomicMin(&fr[a].x, hl);
+        }
+        if (st.do_max && hh >= f[a].y && !is_nan_bits(hi[a])) {
+            atomicMax(&kr[a].y, kh);
+            if (hh > f[a].y) atomicMax(&fr[a].y, hh);
+        }
+    }
+}
+
+// Bin b's f64 filter record (st.mmf set), FltPairs<A_CT> pairs.
+template <int A_CT>
+__device__ __forceinline__ void load_filter(const StateDesc& st, int A, int64_t b, int2* f) {
+    const int2* fr = static_cast<const int2*>(st.mmf) + b * filter_record_pairs(st.n_attrs);
+    load_key_record(fr, f, filter_record_pairs(A));
+}
+
 template <typename T, int A_CT>
 __device__ __forceinline__ void commit_minmax(const StateDesc& st, int A, int64_t b, const T* lo,
                                               const T* hi) {
@@ -634,23 +665,9 @@ __device__ __forceinline__ void commit_minmax(const StateDesc& st, int A, int64_
     using K2 = typename KO::K2;
     if constexpr (sizeof(T) == 8) {
         if (st.mmf) {
-            constexpr int FP = FltPairs<A_CT>::value;
-            int2 f[FP];
-            int2* fr = static_cast<int2*>(st.mmf) + b * filter_record_pairs(st.n_attrs);
-            load_key_record(fr, f, filter_record_pairs(A));
-            K2* kr = static_cast<K2*>(st.mmk) + b * key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
-            for (int a = 0; a < A; ++a) {
-                const long long kl = KO::key(lo[a]), kh = KO::key(hi[a]);
-                const int hl = (int)(kl >> 32), hh = (int)(kh >> 32);  // order preserving
-                if (st.do_min && hl <= f[a].x && !is_nan_bits(lo[a])) {
-                    atomicMin(&kr[a].x, kl);
-                    if (hl < f[a].x) atomicMin(&fr[a].x, hl);
-                }
-                if (st.do_max && hh >= f[a].y && !is_nan_bits(hi[a])) {
-                    atomicMax(&kr[a].y, kh);
-                    if (hh > f[a].y) atomicMax(&fr[a].y, hh);
-                }
-            }
+            int2 f[FltPairs<A_CT>::value];
+            load_filter<A_CT>(st, A, b, f);
+            apply_filtered_minmax<A_CT>(st, A, b, lo, hi, f);
             return;
         }
     }
@@ -683,12 +700,76 @@ __device__ __forceinline__ void commit_minmax(const StateDesc& st, int A, int64_
     }
 }
 
+// A value the bulk record reduction carries: zero or a normal finite
+// double. Subnormal, infinite and NaN values go to the record's element
+// through a plain FP64 reduction instead, so they behave exactly as on every
+// other path. Integer tests on the bits (no FP64 compare).
+__device__ __forceinline__ bool record_plain(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const unsigned e = (unsigned)(u >> 52) & 0x7ffu;
+    return (e - 1u) < 0x7feu || (u << 1) == 0ull;
+}
+
+// One bulk reduction of the RD doubles vals into dst (16-byte aligned, RD
+// even): the copy engine adds the whole record element-wise in L2 as one
+// operation. The values are staged in this thread's shared-memory slot
+// (16-byte aligned, RD doubles), which is rewritten only once the thread's
+// previous reduction has read it.
+template <int RD>
+__device__ __forceinline__ void record_reduce(double* dst, double* slot, const double* vals) {
+    static_assert(RD % 2 == 0, "records are whole 16-byte pieces");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < RD; k += 2) *reinterpret_cast<double2*>(slot + k) = make_double2(vals[k], vals[k + 1]);
+    // the generic-proxy stores must be visible to the async proxy's read
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;"
+                 :: "l"(dst), "r"((unsigned)__cvta_generic_to_shared(slot)), "n"(RD * 8)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Wait until every bulk reduction this thread issued has completed (before
+// the thread exits: its slot lives in the CTA's shared memory).
+__device__ __forceinline__ void record_drain() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Count cnt and the FP64 sums s of bin b: one bulk reduction of the bin's
+// count-and-sums record when the caller passes a slot (st.rec set, 1..
+// kRecMaxAttr attributes known at compile time), else 1 + A reductions.
+template <int A_CT>
+__device__ __forceinline__ void commit_count_sums(const StateDesc& st, int A, int b, unsigned long long cnt,
+                                                  const double* s, double* slot) {
+    if constexpr (A_CT >= 1 && A_CT <= kRecMaxAttr) {
+        if (slot) {
+            constexpr int RD = (A_CT + 2) & ~1;
+            double* dst = st.rec + (int64_t)b * RD;
+            double r[RD];
+            r[0] = (double)cnt;  // exact: cnt <= 32
+#pragma unroll
+            for (int a = 0; a < A_CT; ++a) {
+                const bool plain = record_plain(s[a]);
+                r[1 + a] = plain ? s[a] : 0.0;
+                if (!plain) atomicAdd(dst + 1 + a, s[a]);
+            }
+#pragma unroll
+            for (int k = 1 + A_CT; k < RD; ++k) r[k] = 0.0;
+            record_reduce<RD>(dst, slot, r);
+            return;
+        }
+    }
+    atomicAdd(&st.count[b], cnt);
+    if (st.do_sum)
+        for (int a = 0; a < A; ++a) atomicAdd(&st.sum[a][b], s[a]);
+}
+
 // Combine the lanes of the calling warp that share bin b (b >= 0) and let
 // the lowest such lane update the global mesh. Every lane of the warp must
-// call it (b = -1 for lanes without an in-bounds particle).
+// call it (b = -1 for lanes without an in-bounds particle). slot: this
+// thread's record staging slot when the count and sums go out as records
+// (st.rec), else null.
 template <typename T, int A_CT>
 __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, const T* v,
-                                            bool aggregate) {
+                                            bool aggregate, double* slot = nullptr) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned peers = aggregate ? __match_any_sync(full, b) : (1u << lane);
@@ -697,9 +778,10 @@ __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, c
     if (!aggregate || __all_sync(full, alone || b < 0)) {
         // no two lanes share a bin: skip the combining shuffles
         if (b < 0) return;
-        atomicAdd(&st.count[b], 1ull);
-        if (st.do_sum)
-            for (int a = 0; a < A; ++a) atomicAdd(&st.sum[a][b], (double)v[a]);
+        double vs[A_CT > 0 ? A_CT : kMaxAttr];
+        if (st.do_sum)  // (a record slot implies sums)
+            for (int a = 0; a < A; ++a) vs[a] = (double)v[a];
+        commit_count_sums<A_CT>(st, A, b, 1ull, vs, slot);
         commit_minmax<T, A_CT>(st, A, b, v, v);
         return;
     }
@@ -734,9 +816,7 @@ __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, c
         }
     }
     if (b < 0 || lane != leader) return;
-    atomicAdd(&st.count[b], (unsigned long long)cnt);
-    if (st.do_sum)
-        for (int a = 0; a < A; ++a) atomicAdd(&st.sum[a][b], s[a]);
+    commit_count_sums<A_CT>(st, A, b, (unsigned long long)cnt, s, slot);
     // +inf / -inf where the group holds no non-NaN value: an atomic with them
     // changes nothing, and the direct form skips them
     commit_minmax<T, A_CT>(st, A, b, lo, hi);

@@ -92,6 +92,15 @@ struct StateDesc {
     // record's keys (a key whose top half is above the filter's min cannot
     // lower the min). Only the keys that pass reach the records.
     void* mmf;
+    // Optional count-and-sums records (global strategy, 1..kRecMaxAttr
+    // attributes with sums): per bin record_doubles(n_attrs) doubles {count,
+    // sum of attribute 0, ..., zero padding}, 16-byte aligned, so that one
+    // particle's count and sums reach L2 as one bulk reduction of the whole
+    // record instead of 1 + n_attrs separate reductions. The count is held
+    // as a double: adding 1.0 to an integer-valued double is exact below
+    // 2^53. When set, the particle pass updates these instead of count/sum
+    // and k_finalize writes count and sum from them.
+    double* rec;
     int64_t bins;
     int32_t n_attrs;
     int32_t do_sum;  // sums needed (SUM or AVG requested)
@@ -100,6 +109,14 @@ struct StateDesc {
     int32_t do_avg;
     int32_t pad;
 };
+
+// Attribute counts whose count-and-sums records the global kernel handles.
+constexpr int kRecMaxAttr = 4;
+
+// Doubles per count-and-sums record: the count, one sum per attribute,
+// rounded up to whole 16-byte pieces (a bulk reduction moves multiples of
+// 16 bytes).
+__host__ __device__ __forceinline__ int record_doubles(int n_attrs) { return (n_attrs + 2) & ~1; }
 
 // Key pairs per bin record of StateDesc::mmk: a record of at most 16 bytes is
 // padded to 16 (one 128-bit load), a longer one to whole 32-byte pieces

@@ -51,7 +51,12 @@ __global__ void k_init_state(StateDesc st, T* bounds_acc) {
         bounds_acc[2] = pos_inf<T>();
         bounds_acc[3] = neg_inf<T>();
     }
-    for (int64_t b = t0; b < B; b += stride) st.count[b] = 0ull;
+    if (st.rec) {  // count and sums live in the records until k_finalize
+        const int64_t nd = B * record_doubles(st.n_attrs);
+        for (int64_t q = t0; q < nd; q += stride) st.rec[q] = 0.0;
+    } else {
+        for (int64_t b = t0; b < B; b += stride) st.count[b] = 0ull;
+    }
     if (st.mmk) {
         using KO = KeyOf<T>;
         typename KO::K2 init;
@@ -67,7 +72,7 @@ __global__ void k_init_state(StateDesc st, T* bounds_acc) {
         for (int64_t q = t0; q < pairs; q += stride) fp[q] = make_int2(INT_MAX, INT_MIN);
     }
     for (int a = 0; a < st.n_attrs; ++a) {
-        if (st.do_sum)
+        if (st.do_sum && !st.rec)
             for (int64_t b = t0; b < B; b += stride) st.sum[a][b] = 0.0;
         if (st.mmk) continue;
         if (st.do_min) {
@@ -232,17 +237,28 @@ __global__ void k_grid_setup(GridDesc host_desc, const T* bounds_acc, GridDesc* 
 // ------------------------------------------------------------------ finalise
 // avg = sum / count in FP64 (round-to-nearest, bin_average); empty bins get
 // the quiet NaN 0x7ff8000000000000.
-// With key state (st.mmk), also writes min and max from their keys.
+// With key state (st.mmk), also writes min and max from their keys; with
+// count-and-sums records (st.rec), count and sum from the records.
 template <typename T>
 __global__ void k_finalize(StateDesc st) {
     const int64_t B = st.bins;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
     using KO = KeyOf<T>;
+    const int rd = record_doubles(st.n_attrs);
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += stride) {
-        unsigned long long c = st.do_avg ? st.count[b] : 0ull;
+        unsigned long long c;
+        const double* r = st.rec ? st.rec + b * rd : nullptr;
+        if (r) {
+            // the record's count is an integer-valued double below 2^53
+            c = (unsigned long long)r[0];
+            st.count[b] = c;
+        } else {
+            c = st.do_avg ? st.count[b] : 0ull;
+        }
         for (int a = 0; a < st.n_attrs; ++a) {
-            if (st.do_avg) st.avg[a][b] = c ? bin_average(st.sum[a][b], c) : qnan;
+            if (r) st.sum[a][b] = r[1 + a];
+            if (st.do_avg) st.avg[a][b] = c ? bin_average(r ? r[1 + a] : st.sum[a][b], c) : qnan;
             if (st.mmk) {
                 const int rp = key_record_pairs(st.n_attrs, (int)sizeof(typename KO::K));
                 const auto k = static_cast<const typename KO::K2*>(st.mmk)[b * rp + a];

@@ -6,7 +6,11 @@
 // (executed in L2, not on the SM's FP64 pipe), and min/max atomics only
 // when a plain read of the current value shows the particle would change
 // it (min only falls and max only rises, so a stale read is safe: it can
-// only let through an atomic that turns out to be unnecessary). Lanes of a
+// only let through an atomic that turns out to be unnecessary). With
+// count-and-sums records (StateDesc::rec) the count and the sums of a
+// particle go to L2 as one bulk reduction of the bin's record (measured on
+// GB300: 78 G particles/s against 36 G/s for four separate reductions per
+// particle into the same 1M bins of a centrally concentrated set). Lanes of a
 // warp that hit the same bin are combined first (__match_any_sync) so a
 // cluster of particles costs one set of atomics per warp, not per lane.
 // With a window (BinArgs::win_*), k_window.cu's kernel runs instead.
@@ -74,6 +78,10 @@ __global__ void __launch_bounds__(NT) k_bin_global(BinArgs args, int64_t head, i
     const StateDesc& st = args.st;
     GBinner<T> binner;
     binner.init(g);
+    // count-and-sums records: each thread stages its record in its own slot
+    constexpr int RDS = (A_CT >= 1 && A_CT <= kRecMaxAttr) ? ((A_CT + 2) & ~1) : 2;
+    __shared__ __align__(16) double rec_slots[NT * RDS];
+    double* const slot = (A_CT >= 1 && A_CT <= kRecMaxAttr && st.rec) ? rec_slots + threadIdx.x * RDS : nullptr;
 
     const T* __restrict__ X = static_cast<const T*>(args.x);
     const T* __restrict__ Y = static_cast<const T*>(args.y);
@@ -97,7 +105,7 @@ __global__ void __launch_bounds__(NT) k_bin_global(BinArgs args, int64_t head, i
                 for (int a = 0; a < A; ++a)
                     v[a] = static_cast<const T*>(args.a[a])[i * (args.sa[a] > 1 ? args.sa[a] : 1)];
             }
-            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0);
+            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0, slot);
         }
     };
     scalar_range(0, head);
@@ -133,9 +141,10 @@ __global__ void __launch_bounds__(NT) k_bin_global(BinArgs args, int64_t head, i
                     for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(args.a[a])[i];
                 }
             }
-            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0);
+            warp_commit<T, A_CT>(st, A, b, v, args.aggregate != 0, slot);
         }
     }
+    if (slot) record_drain();
 }
 
 template <typename T>

@@ -674,6 +674,7 @@ size_t bn::request_temp_bytes(const bn_context* c, const bn_block& b, int dtype,
         if (want_max && o->max[a].device == BN_HOST) t += r256((size_t)B * es);
         if (want_avg && o->avg[a].device == BN_HOST) t += r256((size_t)B * 8);
     }
+    if (A >= 1 && A <= kRecMaxAttr && (want_sum || want_avg)) t += r256((size_t)record_doubles(A) * B * 8);
     if (A > 0 && (want_min || want_max)) {
         t += r256((size_t)key_record_pairs(A, (int)es) * B * 2 * es);
         if (dtype == BN_F64 && A >= 3) t += r256((size_t)filter_record_pairs(A) * B * sizeof(int2));
@@ -874,6 +875,13 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
                 if (!sd.mmf) return cuda_fail(plan.err, "cudaMallocAsync(min/max filter)");
             }
         }
+        // the global strategy's count and sums as one record per bin: one
+        // bulk reduction per particle instead of 1 + n_attrs
+        if ((strat == BN_STRATEGY_GLOBAL || trial) && !accumulate && sd.do_sum && n_attrs >= 1 &&
+            n_attrs <= kRecMaxAttr) {
+            sd.rec = static_cast<double*>(plan.alloc((size_t)record_doubles(n_attrs) * B * sizeof(double)));
+            if (!sd.rec) return cuda_fail(plan.err, "cudaMallocAsync(count-and-sums records)");
+        }
         if (strat == BN_STRATEGY_PRIVATE && private_smem_bytes(args, c->smem_optin) == 0)
             return fail(BN_ERR_INVALID_ARG, "BN_STRATEGY_PRIVATE: the mesh does not fit in shared memory");
         const bool sort_ok = sort_plan(args, c->smem_optin, &sortd);
@@ -930,6 +938,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         float best = -1.0f;
         Cand win{strat, args.aggregate};
         std::string times;
+        StateDesc last_st = sd;  // the state the last trial pass wrote
         if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
             for (const Cand& cd : cands) {
                 BinArgs ta = args;
@@ -939,6 +948,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
                 if (cd.strat == BN_STRATEGY_SORT || (cd.strat == BN_STRATEGY_PRIVATE && dtype != BN_F64))
                     ta.st.mmk = nullptr;
                 if (cd.strat != BN_STRATEGY_GLOBAL) ta.st.mmf = nullptr;
+                if (cd.strat != BN_STRATEGY_GLOBAL) ta.st.rec = nullptr;
                 auto pass = [&]() {
                     return cd.strat == BN_STRATEGY_PRIVATE ? launch_bin_private(kc, ta)
                            : cd.strat == BN_STRATEGY_SORT  ? launch_bin_sort(kc, ta, sortd, sort_scratch)
@@ -946,6 +956,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
                 };
                 // one untimed pass first: the first launch of a kernel also
                 // loads its module, which must not count against it
+                last_st = ta.st;
                 e = launch_init_state(kc, dtype, ta.st, nullptr);
                 if (e == cudaSuccess) e = pass();
                 if (e == cudaSuccess) e = launch_init_state(kc, dtype, ta.st, nullptr);
@@ -978,7 +989,10 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
             const int rx = grid->res[0], ry = grid->res[1];
             if (wnx >= 8 && wny >= 8 && (int64_t)wnx * wny < B) {
                 std::vector<unsigned long long> cnt((size_t)B);
-                e = cudaEventSynchronize(e1);
+                // counts kept in count-and-sums records reach the count array
+                // through the finalise kernel
+                if (last_st.rec) e = launch_finalize(kc, last_st, dtype);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(plan.stream);
                 if (e == cudaSuccess)
                     e = cudaMemcpy(cnt.data(), sd.count, (size_t)B * 8, cudaMemcpyDeviceToHost);
                 if (e == cudaSuccess) {
@@ -1011,6 +1025,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
                         ta.win_y0 = wbest[1];
                         ta.win_nx = wnx;
                         ta.win_ny = wny;
+                        ta.st.rec = nullptr;  // the window kernel updates count and sum directly
                         if (e0) cudaEventDestroy(e0);
                         if (e1) cudaEventDestroy(e1);
                         e0 = e1 = nullptr;
@@ -1067,6 +1082,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         }
         if (strat == BN_STRATEGY_SORT || (strat == BN_STRATEGY_PRIVATE && dtype != BN_F64)) sd.mmk = nullptr;
         if (strat != BN_STRATEGY_GLOBAL && strat != BN_STRATEGY_HYBRID) sd.mmf = nullptr;
+        if (strat != BN_STRATEGY_GLOBAL) sd.rec = nullptr;
         args.st = sd;
         e = launch_init_state(kc, dtype, sd, nullptr);
         if (e != cudaSuccess) return cuda_fail(e, "init kernel");
@@ -1086,7 +1102,7 @@ bn_status bn::enqueue_bin(bn_context* c, Plan& plan, const bn_buffer* x, const b
         }
         if (e != cudaSuccess) return cuda_fail(e, "binning kernel");
     }
-    if (want_avg || sd.mmk) {
+    if (want_avg || sd.mmk || sd.rec) {
         e = launch_finalize(kc, sd, dtype);
         if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
     }

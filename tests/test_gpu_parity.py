@@ -312,6 +312,61 @@ def test_special_values(bn, ctx, dtype, strategy):
     check(w, run_gpu(ctx, w, flags=flags), TOL_F64 if dtype == np.float64 else TOL_F32C)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("agg", ["AGG_ON", "AGG_OFF"])
+def test_global_record_sums_edge_values(bn, ctx, dtype, agg):
+    """Global strategy, whose count and sums reach L2 as one bulk reduction of
+    each bin's record: bins holding only subnormal values, normal values that
+    cancel through the subnormal range, infinities, NaN and signed zeros,
+    several warps of particles per bin. Each of these sums is exact in any
+    order of addition, so it must equal the oracle's bit for bit."""
+    rng = np.random.default_rng(41)
+    per, nb = 700, 8
+    tiny = float(np.finfo(np.float64).smallest_subnormal)  # 2^-1074
+    half_min = 2.0 ** -1023
+    f = np.finfo(dtype)
+
+    def case(k):
+        if k == 0:  # subnormal (f64) / smallest f32 subnormal multiples
+            unit = tiny if dtype == np.float64 else float(f.smallest_subnormal)
+            return rng.integers(-50, 51, per) * unit
+        if k == 1:
+            # normal values 3u, -2u, 4u (u = 2^-1023 for f64, 2^-127 for f32)
+            # in random order: the partial sums cross zero and the subnormal
+            # range, and the total is u, itself subnormal
+            unit = half_min if dtype == np.float64 else 2.0 ** -127
+            return rng.permutation(np.array([3.0] * 279 + [-2.0] * 420 + [4.0])) * unit
+        if k == 2:
+            v = rng.normal(0, 1, per)
+            v[rng.integers(per)] = np.inf
+            return v
+        if k == 3:
+            v = rng.normal(0, 1, per)
+            v[:2] = [np.inf, -np.inf]
+            return v
+        if k == 4:
+            v = rng.normal(0, 1, per)
+            v[rng.integers(per)] = np.nan
+            return v
+        if k == 5:
+            return np.full(per, -0.0)
+        return rng.normal(0, 1, per)
+
+    xs, ys, cols = [], [], [[], [], []]
+    for b in range(nb - 1):  # the last bin stays empty
+        xs.append(np.full(per, (b % 4 + 0.5) / 4))
+        ys.append(np.full(per, (b // 4 + 0.5) / 2))
+        for a in range(3):
+            cols[a].append(case((b + 2 * a) % (nb - 1)))
+    p = rng.permutation(per * (nb - 1))
+    x = np.concatenate(xs)[p].astype(dtype)
+    y = np.concatenate(ys)[p].astype(dtype)
+    attrs = [np.concatenate(c)[p].astype(dtype) for c in cols]
+    w = workloads.Workload("record-edges", x, y, attrs, (0.0, 0.0), (1.0, 1.0), (4, 2))
+    flags = bn.STRATEGY_GLOBAL | getattr(bn, agg)
+    check(w, run_gpu(ctx, w, flags=flags), TOL_F64 if dtype == np.float64 else TOL_F32C, label=agg)
+
+
 F64_GRIDS = [
     ((-10.0, -10.0), (10.0, 10.0), (1024, 1024)),
     ((-1.3, 0.1), (2.7, 0.35), (37, 5)),
