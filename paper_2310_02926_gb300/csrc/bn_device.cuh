@@ -710,17 +710,17 @@ __device__ __forceinline__ bool record_plain(double v) {
     return (e - 1u) < 0x7feu || (u << 1) == 0ull;
 }
 
-// One bulk reduction of the RD doubles vals into dst (16-byte aligned, RD
-// even): the copy engine adds the whole record element-wise in L2 as one
-// operation. The values are staged in this thread's shared-memory slot
-// (16-byte aligned, RD doubles), which is rewritten only once the thread's
-// previous reduction has read it.
-template <int RD>
-__device__ __forceinline__ void record_reduce(double* dst, double* slot, const double* vals) {
-    static_assert(RD % 2 == 0, "records are whole 16-byte pieces");
+// Bulk reduction of a staged record: the copy engine adds the RD doubles of
+// this thread's shared-memory slot (16-byte aligned) element-wise into dst
+// (16-byte aligned, RD even) in L2, as one operation. record_slot_ready()
+// must come before the slot is written: it returns once the thread's
+// previous reduction has read the slot.
+__device__ __forceinline__ void record_slot_ready() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-#pragma unroll
-    for (int k = 0; k < RD; k += 2) *reinterpret_cast<double2*>(slot + k) = make_double2(vals[k], vals[k + 1]);
+}
+template <int RD>
+__device__ __forceinline__ void record_reduce(double* dst, const double* slot) {
+    static_assert(RD % 2 == 0, "records are whole 16-byte pieces");
     // the generic-proxy stores must be visible to the async proxy's read
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;"
@@ -734,26 +734,30 @@ __device__ __forceinline__ void record_reduce(double* dst, double* slot, const d
 __device__ __forceinline__ void record_drain() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Count cnt and the FP64 sums s of bin b: one bulk reduction of the bin's
-// count-and-sums record when the caller passes a slot (st.rec set, 1..
-// kRecMaxAttr attributes known at compile time), else 1 + A reductions.
+// count-and-sums record when the caller passes a slot (st.rec set, the
+// attribute count known at compile time), else 1 + A reductions.
 template <int A_CT>
 __device__ __forceinline__ void commit_count_sums(const StateDesc& st, int A, int b, unsigned long long cnt,
                                                   const double* s, double* slot) {
-    if constexpr (A_CT >= 1 && A_CT <= kRecMaxAttr) {
+    if constexpr (A_CT >= 1) {
         if (slot) {
             constexpr int RD = (A_CT + 2) & ~1;
             double* dst = st.rec + (int64_t)b * RD;
-            double r[RD];
-            r[0] = (double)cnt;  // exact: cnt <= 32
+            // element k of the record: the count (exact: cnt <= 32), a plain
+            // sum, or 0.0 (padding, and sums that take the FP64 reduction)
+            auto elem = [&](int k) -> double {
+                if (k == 0) return (double)cnt;
+                if (k > A_CT) return 0.0;
+                return record_plain(s[k - 1]) ? s[k - 1] : 0.0;
+            };
 #pragma unroll
-            for (int a = 0; a < A_CT; ++a) {
-                const bool plain = record_plain(s[a]);
-                r[1 + a] = plain ? s[a] : 0.0;
-                if (!plain) atomicAdd(dst + 1 + a, s[a]);
-            }
+            for (int a = 0; a < A_CT; ++a)
+                if (!record_plain(s[a])) atomicAdd(dst + 1 + a, s[a]);
+            record_slot_ready();
 #pragma unroll
-            for (int k = 1 + A_CT; k < RD; ++k) r[k] = 0.0;
-            record_reduce<RD>(dst, slot, r);
+            for (int k = 0; k < RD; k += 2)
+                *reinterpret_cast<double2*>(slot + k) = make_double2(elem(k), elem(k + 1));
+            record_reduce<RD>(dst, slot);
             return;
         }
     }
@@ -778,10 +782,19 @@ __device__ __forceinline__ void warp_commit(const StateDesc& st, int A, int b, c
     if (!aggregate || __all_sync(full, alone || b < 0)) {
         // no two lanes share a bin: skip the combining shuffles
         if (b < 0) return;
-        double vs[A_CT > 0 ? A_CT : kMaxAttr];
-        if (st.do_sum)  // (a record slot implies sums)
-            for (int a = 0; a < A; ++a) vs[a] = (double)v[a];
-        commit_count_sums<A_CT>(st, A, b, 1ull, vs, slot);
+        if constexpr (A_CT >= 1) {
+            if (slot) {  // (a record slot implies sums)
+                double vs[A_CT];
+#pragma unroll
+                for (int a = 0; a < A_CT; ++a) vs[a] = (double)v[a];
+                commit_count_sums<A_CT>(st, A, b, 1ull, vs, slot);
+                commit_minmax<T, A_CT>(st, A, b, v, v);
+                return;
+            }
+        }
+        atomicAdd(&st.count[b], 1ull);
+        if (st.do_sum)
+            for (int a = 0; a < A; ++a) atomicAdd(&st.sum[a][b], (double)v[a]);
         commit_minmax<T, A_CT>(st, A, b, v, v);
         return;
     }

@@ -131,6 +131,9 @@ struct MultiSpec {
 // Particles per tile of the fused pass: every spec of a tile is binned
 // before the next tile, while the tile's columns are still in L1/L2.
 constexpr int kMultiTile = 2048;
+// Attribute counts the fused pass is compiled for (larger counts take the
+// generic kernel, which updates count and sums with separate reductions).
+constexpr int kMultiRecMaxAttr = 10;
 // dev_specs holds n_groups runs of specs; run g has group_size[g] specs of
 // group_attrs[g] attributes each and gets one launch (the kernel is compiled
 // per attribute count so that its per-particle arrays stay in registers).

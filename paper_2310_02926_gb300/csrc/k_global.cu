@@ -65,10 +65,16 @@ template <> struct GBinner<double> {
     }
 };
 
-// 256 threads per CTA (77 registers at three f64 attributes: three CTAs
-// per SM; capping at 64 registers for four was measured slower).
+// 256 threads per CTA. Up to four attributes: at most 64 registers, four
+// CTAs per SM (at 5e7 Plummer particles, f64, three attributes: 1.157 ms
+// against 1.249 ms for three CTAs per SM at 80 registers; the kernel waits
+// on latency, and more warps hide it). The generic kernel (any attribute
+// count, values through local memory): three CTAs per SM.
+template <int A_CT>
+constexpr int global_min_ctas() { return (A_CT >= 0 && A_CT <= 4) ? 4 : 3; }
+
 template <typename T, int A_CT, int NT>
-__global__ void __launch_bounds__(NT) k_bin_global(BinArgs args, int64_t head, int64_t groups) {
+__global__ void __launch_bounds__(NT, global_min_ctas<A_CT>()) k_bin_global(BinArgs args, int64_t head, int64_t groups) {
     using V = typename GVec<T>::type;
     constexpr int VN = GVec<T>::N;
     constexpr int AC = A_CT > 0 ? A_CT : kMaxAttr;
@@ -113,9 +119,17 @@ __global__ void __launch_bounds__(NT) k_bin_global(BinArgs args, int64_t head, i
 
     const V* __restrict__ XV = reinterpret_cast<const V*>(X + head);
     const V* __restrict__ YV = reinterpret_cast<const V*>(Y + head);
-    for (int64_t gbase = warp_base; gbase < groups; gbase += nthreads) {
-        const int64_t gi = gbase + (threadIdx.x & 31);
-        const bool live = gi < groups;
+    // Vector part. Fixed attribute counts: each CTA (one wave of resident
+    // CTAs) streams one contiguous range of groups, NT per step. The generic
+    // kernel: a grid-stride loop over warps (measured faster for it).
+    constexpr bool kContig = A_CT >= 0;
+    const int64_t per_cta = ((groups + gridDim.x - 1) / gridDim.x + NT - 1) / NT * NT;
+    const int64_t g_begin = kContig ? min(groups, (int64_t)blockIdx.x * per_cta) : warp_base;
+    const int64_t g_end = kContig ? min(groups, g_begin + per_cta) : groups;
+    const int64_t g_step = kContig ? (int64_t)NT : nthreads;
+    for (int64_t gb = g_begin; gb < g_end; gb += g_step) {
+        const int64_t gi = gb + (kContig ? (int64_t)threadIdx.x : (int64_t)(threadIdx.x & 31));
+        const bool live = gi < g_end;
         V x0, y0;
         V av[A_CT > 0 ? A_CT : 1];
         if (live) {
@@ -174,11 +188,16 @@ static cudaError_t launch_global_t(const KernelCtx& kc, const BinArgs& a) {
     gvector_split<T>(a, &head, &groups);
     const int64_t work = groups > 0 ? groups : a.n;
     const int block = 256;
+    auto kern = k_bin_global<T, A_CT, 256>;
+    // one wave of resident CTAs, each with a contiguous share of the groups
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
+    if (e != cudaSuccess) return e;
     int64_t grid = (work + block - 1) / block;
-    const int64_t cap = (int64_t)kc.num_sms * 8;
+    const int64_t cap = (int64_t)kc.num_sms * (A_CT >= 0 ? (per_sm > 0 ? per_sm : 1) : 8);
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    k_bin_global<T, A_CT, 256><<<(int)grid, block, 0, kc.stream>>>(a, head, groups);
+    kern<<<(int)grid, block, 0, kc.stream>>>(a, head, groups);
     kc.count_launch();
     return cudaGetLastError();
 }

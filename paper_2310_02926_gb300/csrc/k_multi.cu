@@ -7,8 +7,9 @@
 // columns for the tile; the first spec to touch a column brings it from
 // DRAM, the others find it in L1/L2 (a tile of one f64 column is 8 KB), so
 // each column crosses DRAM once however many specs use it. Each spec bins
-// exactly as the global strategy does (same bin index, same commit), so its
-// result equals a bn_bin_particles call on its columns and grid.
+// exactly as the global strategy does (same bin index, same commit, count
+// and sums as one bulk reduction of the bin's record), so its result equals
+// a bn_bin_particles call on its columns and grid.
 #include <cuda_runtime.h>
 
 #include "bn_device.cuh"
@@ -28,7 +29,7 @@ namespace bn {
 // 4.48 to 5.08 ms, so larger counts load one particle per lane.)
 template <typename T, int K>
 __device__ __forceinline__ void multi_tile(const MultiSpec& sp, const Binner<T>& binner, int64_t i0,
-                                           int64_t i1) {
+                                           int64_t i1, double* slot) {
     using V = typename VecOf<T>::type;
     constexpr int VN = VecOf<T>::N;
     constexpr int KC = K > 0 ? K : (K == 0 ? 1 : kMaxAttr);
@@ -73,7 +74,7 @@ __device__ __forceinline__ void multi_tile(const MultiSpec& sp, const Binner<T>&
                             for (int a = 0; a < K; ++a) v[a] = vget<T>(av[a], j);
                         }
                     }
-                    warp_commit<T, K>(sp.st, A, b, v, agg);
+                    warp_commit<T, K>(sp.st, A, b, v, agg, slot);
                 }
             }
             s0 = g1 * VN;
@@ -93,17 +94,20 @@ __device__ __forceinline__ void multi_tile(const MultiSpec& sp, const Binner<T>&
                 for (int a = 0; a < A; ++a) v[a] = static_cast<const T*>(sp.a[a])[i];
             }
         }
-        warp_commit<T, K>(sp.st, A, b, v, agg);
+        warp_commit<T, K>(sp.st, A, b, v, agg, slot);
     }
 }
 
 // All specs of one launch have K attributes (the host groups them).
 template <typename T, int K>
-__global__ void __launch_bounds__(256) k_bin_multi(const MultiSpec* __restrict__ specs, int n_specs,
+__global__ void __launch_bounds__(256, 2) k_bin_multi(const MultiSpec* __restrict__ specs, int n_specs,
                                                    int64_t n) {
     // every spec's binner, built once per CTA
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ MultiSpec cur;
+    // count-and-sums records (StateDesc::rec): each thread's staging slot
+    constexpr int RDS = K >= 1 ? ((K + 2) & ~1) : 2;
+    __shared__ __align__(16) double rec_slots[256 * RDS];
     Binner<T>* binners = reinterpret_cast<Binner<T>*>(smem);
     for (int s = threadIdx.x; s < n_specs; s += blockDim.x) {
         const GridDesc g = *specs[s].grid;
@@ -130,9 +134,10 @@ __global__ void __launch_bounds__(256) k_bin_multi(const MultiSpec* __restrict__
                     dst[w] = src[w];
             }
             __syncthreads();
-            multi_tile<T, K>(cur, binner, i0, i1);
+            multi_tile<T, K>(cur, binner, i0, i1, (K >= 1 && cur.st.rec) ? rec_slots + threadIdx.x * RDS : nullptr);
         }
     }
+    if (K >= 1) record_drain();
 }
 
 template <typename T, int K>

@@ -1236,6 +1236,12 @@ static bn_status enqueue_multi(bn_context* c, Plan& plan, const bn_buffer* cols,
                                 dtype_size(dtype));
             if (!sd.mmk) return cuda_fail(plan.err, "cudaMallocAsync(min/max keys)");
         }
+        // count and sums as one record per bin (one bulk reduction per
+        // particle and spec), for the counts the kernel is compiled for
+        if (sd.do_sum && A >= 1 && A <= kMultiRecMaxAttr) {
+            sd.rec = static_cast<double*>(plan.alloc((size_t)record_doubles(A) * B * sizeof(double)));
+            if (!sd.rec) return cuda_fail(plan.err, "cudaMallocAsync(count-and-sums records)");
+        }
         e = launch_init_state(kc, dtype, sd, nullptr);
         if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     }
@@ -1268,7 +1274,7 @@ static bn_status enqueue_multi(bn_context* c, Plan& plan, const bn_buffer* cols,
     }
     if (e != cudaSuccess) return cuda_fail(e, "fused multi-grid kernel");
     for (int k = 0; k < n_specs; ++k)
-        if (want_avg || hs[k].st.mmk) {
+        if (want_avg || hs[k].st.mmk || hs[k].st.rec) {
             e = launch_finalize(kc, hs[k].st, dtype);
             if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
         }
