@@ -180,7 +180,9 @@ enum {
     /* Accumulation strategy (bits 12-15); AUTO lets the library choose. */
     BN_STRATEGY_AUTO = 0u << 12,
     BN_STRATEGY_PRIVATE = 1u << 12, /* per-CTA shared-memory copy of the mesh */
-    BN_STRATEGY_GLOBAL = 2u << 12,  /* warp-aggregated atomics into the global mesh */
+    BN_STRATEGY_GLOBAL = 2u << 12,  /* atomics into the global mesh (count and sums of a
+                                      * particle as one bulk reduction of the bin's record,
+                                      * for 1-4 attributes; warp aggregation optional) */
     BN_STRATEGY_SORT = 3u << 12,    /* tile sort by bin + segmented reduce */
     /* Global atomics with a shared-memory window: every CTA keeps the counts
      * and sums of a rectangle of the densest bins in shared memory (sums as
