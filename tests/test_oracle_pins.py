@@ -293,6 +293,41 @@ def test_nan_attribute_skipped_by_min_max_and_propagates_to_sum():
     assert r["min"][0][0] == -1.0 and r["max"][0][0] == 2.0
 
 
+def test_sums_exact_at_the_bottom_of_the_range():
+    """Sums of subnormal values, and of normal values whose partial sums cross
+    zero and the subnormal range, are exact in FP64 (every partial sum is a
+    small multiple of 2^-1074): the oracle must return the exact rational
+    sum. Signed zeros add to +0.0; an infinity dominates; +inf and -inf give
+    NaN (IEEE 754 addition)."""
+    rng = np.random.default_rng(43)
+    tiny = 2.0 ** -1074
+    cases = {
+        "subnormal": rng.integers(-50, 51, 700) * tiny,
+        "cancel": rng.permutation(np.array([3.0] * 279 + [-2.0] * 420 + [4.0])) * 2.0 ** -1023,
+        "zeros": np.where(rng.random(300) < 0.5, -0.0, 0.0),
+        "neg_zeros": np.full(300, -0.0),
+        "inf": np.concatenate([rng.normal(0, 1, 50), [np.inf]]),
+        "inf_minus_inf": np.concatenate([rng.normal(0, 1, 50), [np.inf, -np.inf]]),
+    }
+    for name, a in cases.items():
+        x = np.full(a.size, 0.5)
+        y = np.full(a.size, 0.5)
+        r = oracle.bin_particles(x, y, [a], (0, 0), (1, 1), (1, 1))
+        got = r["sum"][0][0]
+        if name == "inf":
+            assert got == np.inf, name
+        elif name == "inf_minus_inf":
+            assert math.isnan(got), name
+        else:
+            exact = sum((Fraction(float(v)) for v in a), Fraction(0))
+            assert Fraction(float(got)) == exact, name
+            if exact == 0:
+                assert math.copysign(1.0, got) == 1.0, f"{name}: a zero sum is +0.0"
+    # the cancellation case ends on 2^-1023, itself subnormal
+    r = oracle.bin_particles(np.full(700, 0.5), np.full(700, 0.5), [cases["cancel"]], (0, 0), (1, 1), (1, 1))
+    assert r["sum"][0][0] == 2.0 ** -1023
+
+
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 def test_min_max_in_total_order_for_signed_zero(dtype):
     x = np.array([0.1, 0.2], dtype)
